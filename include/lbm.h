@@ -1,0 +1,197 @@
+/*
+ * liblbm: progressive-mesh, two-component pseudo-potential lattice
+ * Boltzmann time step (D3Q19) on one GB300 GPU (sm_103a).
+ *
+ * Method: Duchateau et al., "A Progressive Mesh Method for Physical
+ * Simulations Using Lattice Boltzmann Method on Single-Node multi-GPU
+ * Architectures" (arXiv:1510.03560).
+ *   - SRT-BGK lattice Boltzmann equation and equilibrium: Sec. 2.1, Eqs. 1-5.
+ *   - Peng-Robinson EOS, pseudo-potential, cohesion, inter-component and
+ *     extra (gravity, fluid-solid) forces, exact-difference forcing:
+ *     Sec. 2.2, Eqs. 6-12.
+ *   - Progressive mesh: sub-domains created where the velocity-change
+ *     criterion of Eq. 13 exceeds S on the boundary of the meshed region:
+ *     Sec. 4.1-4.3, Fig. 4.
+ *   - Throughput metric (MLUPS): Sec. 5.3, Eq. 16.
+ *
+ * The sub-domain (the unit of meshing) is an 8 x 8 x 8 block of cells.  A
+ * block is "active" once meshed; blocks are never removed.  Unmeshed
+ * blocks behave as a resting ambient at the densities rho_amb.
+ *
+ * Conventions shared by every entry point:
+ *   - Grid arrays are dense, x fastest: index x + nx * (y + ny * z).
+ *   - Per-component arrays are [ncomp][nz][ny][nx]; velocity arrays
+ *     [ncomp][3][nz][ny][nx].
+ *   - Cell types: 0 fluid, 1 solid (halfway bounce-back wall), 2 held (its
+ *     populations stay at the initial equilibrium: inlets, outlets).
+ *   - Block ids are linear, x fastest: bx + nbx * (by + nby * bz), with
+ *     nbx = nx / 8 and so on.
+ *   - Host pointers belong to the caller and are only read or written
+ *     during the call; the library never keeps them.
+ *   - The context owns all device memory it allocates (through the
+ *     caller's allocator when one is given) and frees it in lbm_destroy.
+ *   - Every function returns LBM_OK or an error code; the message of the
+ *     last error is available from lbm_last_error().  No exception or
+ *     process exit crosses this interface.  A context is used by one host
+ *     thread at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL 1  /* invalid argument or parameter */
+#define LBM_ENOMEM 2  /* block pool full, or a device allocation failed */
+#define LBM_ECUDA 3   /* a CUDA runtime call failed */
+#define LBM_ESTATE 4  /* call out of order (e.g. lbm_step before lbm_set_geometry) */
+
+#define LBM_CELL_FLUID 0
+#define LBM_CELL_SOLID 1
+#define LBM_CELL_HELD 2
+
+#define LBM_BLOCK_EDGE 8 /* cells per block edge */
+#define LBM_Q 19         /* D3Q19 populations per component */
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Device allocator: returns a device pointer of at least `bytes` bytes
+ * (256-byte aligned) or NULL; `user` is lbm_params.alloc_user. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *user);
+typedef void (*lbm_free_fn)(void *ptr, void *user);
+
+typedef struct lbm_params {
+    int nx, ny, nz;      /* grid, each a positive multiple of 8 */
+    int ncomp;           /* 1 or 2; component 0 follows the Peng-Robinson EOS,
+                            component 1 is an ideal gas (p = rho / 3, psi = 0) */
+    int periodic[3];     /* per axis: 1 wraps around, 0 ends in solid cells */
+    int progressive;     /* 1: progressive mesh (Sec. 4); 0: static mesh, every
+                            block holding a non-solid cell meshed from the start */
+    double tau;          /* BGK relaxation time, Eq. 1 (> 0.5) */
+    double beta;         /* weighting term of Eq. 8 (the paper uses 1.16) */
+    double pr_a, pr_b, pr_R, pr_omega; /* Peng-Robinson a, b, R, acentric factor, Eq. 7 */
+    double T_over_Tc;    /* temperature as a fraction of Tc = 0.0778 a / (0.45724 b R) */
+    double g_self;       /* g_aa of Eqs. 6 and 8 (< 0 attracts; 0 turns cohesion off) */
+    double g_cross;      /* g_aa' of Eq. 9 (> 0 repels) */
+    double g_ads[2];     /* fluid-solid strength per component: F = -g_ads *
+                            max(0, rho - rho_amb) * sum_i w_i s(x + e_i) e_i */
+    double grav[3];      /* body-force acceleration: F = (rho - rho_ref) * grav */
+    double rho_ref[2];   /* reference density of the body force, per component */
+    double S;            /* threshold of Eq. 13 (>= 0): a block is created when
+                            ||u(t) - u(t-1)||_2 > S at a neighbouring cell */
+    long long max_blocks; /* block-pool capacity in blocks; 0 = every block */
+    lbm_alloc_fn dev_alloc; /* NULL: cudaMallocAsync on `stream` */
+    lbm_free_fn dev_free;
+    void *alloc_user;
+    void *stream;        /* cudaStream_t for every launch and copy; NULL = default */
+} lbm_params;
+
+/* Counters of a context (lbm_get_stats). */
+typedef struct lbm_stats {
+    long long steps;            /* completed time steps */
+    long long active_blocks;    /* blocks meshed now */
+    long long capacity;         /* block-pool capacity */
+    long long total_blocks;     /* blocks of the grid */
+    long long nonsolid_blocks;  /* blocks holding at least one non-solid cell */
+    long long cell_updates;     /* sum over completed steps of 512 x active blocks */
+    long long launches;         /* kernels this context has launched */
+    long long device_bytes;     /* device memory held by the context */
+    double kernel_ms[4];        /* with profiling on: device time per kernel kind
+                                   (0 stream+macro, 1 block creation, 2 force+collide,
+                                   3 other) accumulated over lbm_step calls */
+    long long kernel_launches[4];
+} lbm_stats;
+
+/* Validate `p`, allocate the block pool (capacity x 2 buffers x ncomp x 19 x
+ * 512 floats) and the tables, and return a new context in *out.  Allocates
+ * through p->dev_alloc when given.  Errors: LBM_EINVAL (bad parameter: grid
+ * not a multiple of 8, ncomp not 1 or 2, tau <= 0.5, S < 0, ...; no CUDA
+ * call is made then), LBM_ENOMEM, LBM_ECUDA.  On error *out is NULL. */
+int lbm_create(const lbm_params *p, lbm_ctx **out);
+
+/* Free everything the context holds.  NULL is accepted. */
+int lbm_destroy(lbm_ctx *ctx);
+
+/* Geometry and initial state (Sec. 4.1: the first sub-domains are created
+ * where the fluid starts).
+ *   cell_type  [nz][ny][nx] uint8, values 0..2 (see above)
+ *   rho_init   [ncomp][nz][ny][nx] initial densities
+ *   u_init     [ncomp][3][nz][ny][nx] initial velocities, or NULL for rest
+ *   rho_amb    [ncomp] densities of the resting ambient in unmeshed blocks
+ * The initial populations are the equilibrium of Eq. 2 at (rho_init,
+ * u_init).  Progressive mode meshes every block that holds a non-solid cell
+ * whose initial state differs from the ambient; static mode meshes every
+ * block holding a non-solid cell.  Held cells must sit in meshed blocks or
+ * hold exactly the ambient state.  Resets the step counter.  Errors:
+ * LBM_EINVAL, LBM_ENOMEM (initial blocks exceed the capacity), LBM_ECUDA. */
+int lbm_set_geometry(lbm_ctx *ctx, const uint8_t *cell_type, const float *rho_init,
+                     const float *u_init, const float *rho_amb);
+
+/* Advance `nsteps` time steps and wait for them.  One step: pull
+ * streaming and the macroscopic moments (Eqs. 4-5) on the meshed blocks;
+ * in progressive mode the criterion of Eq. 13 on cells bordering unmeshed
+ * blocks and the creation of the blocks it selects (they start from the
+ * ambient equilibrium and take part in the same step); Peng-Robinson psi
+ * (Eqs. 6-7); forces (Eqs. 8-9, gravity, fluid-solid); forced BGK collision
+ * (Eqs. 10-12).  Errors: LBM_ESTATE (no geometry, or an earlier error),
+ * LBM_ENOMEM (the pool cannot hold the blocks a step creates: the state is
+ * left as it was after the last completed step, and stepping stays refused),
+ * LBM_ECUDA. */
+int lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* lbm_step without the final wait: enqueues the steps on the context's
+ * stream and returns.  Errors raised on the device (LBM_ENOMEM) are
+ * reported by the next lbm_sync. */
+int lbm_step_async(lbm_ctx *ctx, int nsteps);
+
+/* Wait for enqueued work and report its status (as lbm_step). */
+int lbm_sync(lbm_ctx *ctx);
+
+/* Macroscopic fields of component `comp` for the current state: the
+ * density of Eq. 4 and, for fluid cells, the velocity u + F / (2 rho) (the
+ * velocity of the exact-difference forcing scheme), both as the next step
+ * would compute them after streaming.  Held cells report the moments of
+ * their own populations, solid cells 0, cells of unmeshed blocks the
+ * ambient density at rest.  Outputs: host arrays of nx*ny*nz floats (any
+ * of the four may be NULL).  Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA. */
+int lbm_get_macro(lbm_ctx *ctx, int comp, float *rho, float *ux, float *uy, float *uz);
+
+/* Ids of the meshed blocks in ascending order.  Writes min(n, cap) ids to
+ * `ids` (host, may be NULL when cap is 0) and the count to *n. */
+int lbm_active_blocks(lbm_ctx *ctx, int32_t *ids, long long cap, long long *n);
+
+/* Per-component mass, the sum of the populations over every non-solid
+ * cell, unmeshed cells counted at the ambient equilibrium; accumulated in
+ * FP64 on the device in a fixed order.  mass: host array of ncomp doubles. */
+int lbm_mass(lbm_ctx *ctx, double *mass);
+
+/* Post-collision populations of one meshed block, host array
+ * [ncomp][19][512] in the library's velocity order (lbm_velocities), cell
+ * index x + 8 * (y + 8 * z) within the block.  LBM_EINVAL if the block is
+ * not meshed. */
+int lbm_get_block_populations(lbm_ctx *ctx, int32_t block_id, float *out);
+
+/* The library's D3Q19 velocity order: e[3 * i + axis], 19 x 3 ints. */
+int lbm_velocities(int32_t *e);
+
+/* Turn per-kernel device timing on (1) or off (0); on adds a pair of CUDA
+ * events around each launch of lbm_step / lbm_step_async. */
+int lbm_set_profiling(lbm_ctx *ctx, int on);
+
+/* Counters; waits for enqueued work first. */
+int lbm_get_stats(lbm_ctx *ctx, lbm_stats *out);
+
+/* Message of the last error of `ctx`, or of the last failed lbm_create
+ * when ctx is NULL.  Never NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,717 @@
+// Host runtime of liblbm: the C ABI of include/lbm.h.  It owns the context
+// (parameters, block pool, block tables, error state), builds the geometry
+// tables, enqueues the kernels of lbm_kernels.cu and moves results to the
+// host.  Method: arXiv:1510.03560, Sec. 2 (physics) and Sec. 4 (progressive
+// mesh); the per-call references are in include/lbm.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+// The library's velocity order (same table as the kernels).
+constexpr int EV[Q][3] = {
+    {0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {1, 1, 0},  {-1, -1, 0},
+    {1, -1, 0},  {-1, 1, 0},  {0, 0, 1},  {1, 0, 1},  {-1, 0, 1}, {0, 1, 1},  {0, -1, 1},
+    {0, 0, -1},  {-1, 0, -1}, {1, 0, -1}, {0, -1, -1}, {0, 1, -1}};
+
+float weight_f(int i)
+{
+    int n2 = EV[i][0] * EV[i][0] + EV[i][1] * EV[i][1] + EV[i][2] * EV[i][2];
+    return n2 == 0 ? 1.0f / 3.0f : (n2 == 1 ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+
+thread_local char g_create_error[512] = "no error";
+
+struct Event {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct lbm_ctx {
+    lbm_params p{};
+    int device = 0;
+    int sms = 1;
+    int ctas_per_sm = 1;
+    int nbx = 0, nby = 0, nbz = 0;
+    long long nblocks = 0;
+    int capacity = 0;
+    bool geometry = false;
+    long long step = 0;        // completed steps (host view)
+    int sticky = LBM_OK;       // error that refuses further steps
+    char err[512] = "no error";
+    cudaStream_t stream = nullptr;
+    KParams kp{};
+    // device allocations
+    std::vector<void *> allocs;
+    long long device_bytes = 0;
+    double *mass_partial = nullptr;
+    double *mass_out = nullptr;
+    float *stage = nullptr;    // staging buffer (initial state upload, macro download)
+    size_t stage_floats = 0;
+    // host copies of the geometry
+    std::vector<uint32_t> solid_h, held_h;
+    std::vector<int> nonsolid_h;  // non-solid cells per block
+    std::vector<int> slot_of_h;   // at set_geometry (static tables)
+    float rho_amb[2] = {0.f, 0.f};
+    // counters
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<Event> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double kernel_ms[4] = {0, 0, 0, 0};
+    long long kernel_launches[4] = {0, 0, 0, 0};
+};
+
+namespace {
+
+int fail(lbm_ctx *c, int code, const char *fmt, ...)
+{
+    char *dst = c ? c->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CUDA_OR_FAIL(ctx, call)                                                             \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail((ctx), LBM_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+// Keeps the context's device current for the duration of an API call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            ok = false;
+            return;
+        }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void *dev_alloc(lbm_ctx *c, size_t bytes)
+{
+    bytes = (bytes + 255) & ~size_t(255);
+    void *ptr = nullptr;
+    if (c->p.dev_alloc) {
+        ptr = c->p.dev_alloc(bytes, c->p.alloc_user);
+    } else if (cudaMallocAsync(&ptr, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) {
+        c->allocs.push_back(ptr);
+        c->device_bytes += (long long)bytes;
+    }
+    return ptr;
+}
+
+void free_all(lbm_ctx *c)
+{
+    for (void *ptr : c->allocs) {
+        if (c->p.dev_free)
+            c->p.dev_free(ptr, c->p.alloc_user);
+        else
+            cudaFreeAsync(ptr, c->stream);
+    }
+    c->allocs.clear();
+    c->device_bytes = 0;
+}
+
+int validate(const lbm_params *p)
+{
+    if (!p) return fail(nullptr, LBM_EINVAL, "params is NULL");
+    if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || p->nx % EDGE || p->ny % EDGE || p->nz % EDGE)
+        return fail(nullptr, LBM_EINVAL, "grid %dx%dx%d is not a positive multiple of %d", p->nx,
+                    p->ny, p->nz, EDGE);
+    if (p->ncomp != 1 && p->ncomp != 2)
+        return fail(nullptr, LBM_EINVAL, "ncomp must be 1 or 2, got %d", p->ncomp);
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau))
+        return fail(nullptr, LBM_EINVAL, "tau must be > 0.5, got %g", p->tau);
+    if (!(p->S >= 0.0) || !std::isfinite(p->S))
+        return fail(nullptr, LBM_EINVAL, "S must be >= 0, got %g", p->S);
+    if (p->max_blocks < 0) return fail(nullptr, LBM_EINVAL, "max_blocks must be >= 0");
+    if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
+        return fail(nullptr, LBM_EINVAL, "dev_alloc and dev_free must be given together");
+    for (int a = 0; a < 3; ++a)
+        if (p->periodic[a] != 0 && p->periodic[a] != 1)
+            return fail(nullptr, LBM_EINVAL, "periodic[%d] must be 0 or 1", a);
+    if (p->g_self != 0.0 && (p->pr_b <= 0.0 || p->pr_a <= 0.0 || p->pr_R <= 0.0 ||
+                             p->T_over_Tc <= 0.0))
+        return fail(nullptr, LBM_EINVAL, "Peng-Robinson a, b, R and T/Tc must be > 0");
+    long long nb = (long long)(p->nx / EDGE) * (p->ny / EDGE) * (p->nz / EDGE);
+    if (nb > INT32_MAX / 2) return fail(nullptr, LBM_EINVAL, "grid too large");
+    return LBM_OK;
+}
+
+void fill_physics(lbm_ctx *c)
+{
+    const lbm_params &p = c->p;
+    KParams &k = c->kp;
+    k.nbx = c->nbx;
+    k.nby = c->nby;
+    k.nbz = c->nbz;
+    for (int a = 0; a < 3; ++a) k.per[a] = p.periodic[a];
+    k.ncomp = p.ncomp;
+    k.capacity = c->capacity;
+    k.progressive = p.progressive ? 1 : 0;
+    k.omega = (float)(1.0 / p.tau);
+    k.beta = (float)p.beta;
+    k.g_self = (float)p.g_self;
+    k.g_cross = (float)p.g_cross;
+    for (int a = 0; a < 2; ++a) {
+        k.g_ads[a] = (float)p.g_ads[a];
+        k.rho_ref[a] = (float)p.rho_ref[a];
+    }
+    for (int d = 0; d < 3; ++d) k.grav[d] = (float)p.grav[d];
+    k.S2 = (float)(p.S * p.S);
+    // Peng-Robinson constants (Eq. 7): Tc from a and b, theta(T) the
+    // standard alpha function of the acentric factor.
+    double Tc = 0.0778 * p.pr_a / (0.45724 * p.pr_b * p.pr_R);
+    double T = p.T_over_Tc * Tc;
+    double kap = 0.37464 + 1.54226 * p.pr_omega - 0.26992 * p.pr_omega * p.pr_omega;
+    double sq = 1.0 + kap * (1.0 - std::sqrt(T / Tc));
+    k.pr_b = (float)p.pr_b;
+    k.pr_RT = (float)(p.pr_R * T);
+    k.pr_atheta = (float)(p.pr_a * sq * sq);
+    k.psi_scale = p.g_self != 0.0 ? (float)(2.0 / ((1.0 / 3.0) * p.g_self)) : 0.f;
+}
+
+void flush_profile(lbm_ctx *c)
+{
+    for (Event &e : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+            c->kernel_ms[e.kind] += ms;
+            c->kernel_launches[e.kind] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        c->event_pool.push_back(e.a);
+        c->event_pool.push_back(e.b);
+    }
+    c->pending.clear();
+}
+
+cudaEvent_t take_event(lbm_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Launch `fn` with optional timing events around it.
+template <class F>
+cudaError_t timed(lbm_ctx *c, int kind, F &&fn)
+{
+    Event ev{kind, nullptr, nullptr};
+    if (c->profiling) {
+        ev.a = take_event(c);
+        ev.b = take_event(c);
+        if (ev.a) cudaEventRecord(ev.a, c->stream);
+    }
+    cudaError_t e = fn();
+    c->launches += 1;
+    if (c->profiling && ev.a && ev.b) {
+        cudaEventRecord(ev.b, c->stream);
+        c->pending.push_back(ev);
+    }
+    return e;
+}
+
+int persistent_grid(lbm_ctx *c) { return c->sms * c->ctas_per_sm; }
+
+// Read the device control words after the stream is idle.
+int read_ctrl(lbm_ctx *c, Ctrl &out)
+{
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(&out, c->kp.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int enqueue_steps(lbm_ctx *c, int nsteps)
+{
+    const int grid = persistent_grid(c);
+    for (int k = 0; k < nsteps; ++k) {
+        const int t = (int)(c->step + k);
+        CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
+                         return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, grid, c->stream);
+                     }));
+        if (c->p.progressive)
+            CUDA_OR_FAIL(c, timed(c, K_ACTIVATE,
+                                  [&] { return launch_activate(c->kp, t, c->sms, c->stream); }));
+        CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, grid, c->stream); }));
+    }
+    c->step += nsteps;
+    return LBM_OK;
+}
+
+int finish(lbm_ctx *c)
+{
+    Ctrl ctrl;
+    int rc = read_ctrl(c, ctrl);
+    if (rc) return rc;
+    if (c->profiling) flush_profile(c);
+    if (ctrl.status != 0) {
+        c->step = ctrl.fail_step;
+        c->sticky = ctrl.status;
+        if (ctrl.status == LBM_ENOMEM)
+            return fail(c, LBM_ENOMEM,
+                        "block pool full at step %d: %d meshed + %d new blocks > capacity %d",
+                        ctrl.fail_step, ctrl.n_active[ctrl.fail_step & 1],
+                        ctrl.ncand[ctrl.fail_step & 1], c->capacity);
+        return fail(c, ctrl.status, "device error %d at step %d", ctrl.status, ctrl.fail_step);
+    }
+    return LBM_OK;
+}
+
+int active_count(lbm_ctx *c, int *n)
+{
+    Ctrl ctrl;
+    int rc = read_ctrl(c, ctrl);
+    if (rc) return rc;
+    *n = ctrl.n_active[c->step & 1];
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_create(const lbm_params *p, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    c->p = *p;
+    c->stream = (cudaStream_t)p->stream;
+    c->nbx = p->nx / EDGE;
+    c->nby = p->ny / EDGE;
+    c->nbz = p->nz / EDGE;
+    c->nblocks = (long long)c->nbx * c->nby * c->nbz;
+    long long cap = p->max_blocks > 0 ? std::min<long long>(p->max_blocks, c->nblocks) : c->nblocks;
+    c->capacity = (int)cap;
+    auto bail = [&](int code) {
+        snprintf(g_create_error, sizeof g_create_error, "%s", c->err);
+        free_all(c);
+        delete c;
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        fail(c, LBM_ECUDA, "no CUDA device: %s", cudaGetErrorString(cudaGetLastError()));
+        return bail(LBM_ECUDA);
+    }
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    c->ctas_per_sm = max_ctas_per_sm_stream_kernels();
+    fill_physics(c);
+
+    const size_t slot_floats = (size_t)p->ncomp * Q * CELLS;
+    KParams &k = c->kp;
+    k.slot_floats = (int)slot_floats;
+    k.buf_stride = slot_floats * (size_t)c->capacity;
+    struct Want {
+        void **dst;
+        size_t bytes;
+    } want[] = {
+        {(void **)&k.f, 2 * k.buf_stride * sizeof(float)},
+        {(void **)&k.mac, (size_t)c->capacity * MACS * CELLS * sizeof(float)},
+        {(void **)&k.uprev, p->progressive ? (size_t)c->capacity * p->ncomp * 3 * CELLS * sizeof(float) : 0},
+        {(void **)&k.slot_of, (size_t)c->nblocks * sizeof(int)},
+        {(void **)&k.block_of, (size_t)c->capacity * sizeof(int)},
+        {(void **)&k.solid, (size_t)c->nblocks * MASK_WORDS * sizeof(uint32_t)},
+        {(void **)&k.held, (size_t)c->nblocks * MASK_WORDS * sizeof(uint32_t)},
+        {(void **)&k.cand_list, (size_t)c->nblocks * sizeof(int)},
+        {(void **)&k.cand_mark, (size_t)c->nblocks * sizeof(unsigned)},
+        {(void **)&k.ctrl, sizeof(Ctrl)},
+        {(void **)&c->mass_partial, (size_t)c->capacity * 2 * sizeof(double)},
+        {(void **)&c->mass_out, 2 * sizeof(double)},
+    };
+    for (auto &w : want) {
+        if (w.bytes == 0) {
+            *w.dst = nullptr;
+            continue;
+        }
+        *w.dst = dev_alloc(c, w.bytes);
+        if (!*w.dst) {
+            fail(c, LBM_ENOMEM, "device allocation of %zu bytes failed", w.bytes);
+            return bail(LBM_ENOMEM);
+        }
+    }
+    // staging: up to 2048 blocks of [ncomp][4][CELLS] floats at a time
+    c->stage_floats = (size_t)std::min(c->capacity, 2048) * p->ncomp * 4 * CELLS;
+    if (c->stage_floats < 4 * CELLS) c->stage_floats = 4 * CELLS;
+    c->stage = (float *)dev_alloc(c, c->stage_floats * sizeof(float));
+    if (!c->stage) {
+        fail(c, LBM_ENOMEM, "staging allocation failed");
+        return bail(LBM_ENOMEM);
+    }
+    if (cudaMemsetAsync(k.ctrl, 0, sizeof(Ctrl), c->stream) != cudaSuccess) {
+        fail(c, LBM_ECUDA, "memset failed");
+        return bail(LBM_ECUDA);
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return LBM_OK;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    flush_profile(c);
+    free_all(c);
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+    return LBM_OK;
+}
+
+int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init,
+                     const float *u_init, const float *rho_amb)
+{
+    if (!c) return LBM_EINVAL;
+    if (!cell_type || !rho_init || !rho_amb)
+        return fail(c, LBM_EINVAL, "cell_type, rho_init and rho_amb are required");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, LBM_ECUDA, "cannot select device %d", c->device);
+    const lbm_params &p = c->p;
+    const long long ncell = (long long)p.nx * p.ny * p.nz;
+    const int nc = p.ncomp;
+    for (long long i = 0; i < ncell; ++i)
+        if (cell_type[i] > 2) return fail(c, LBM_EINVAL, "cell_type[%lld] = %d", i, cell_type[i]);
+    for (int a = 0; a < nc; ++a) {
+        if (!std::isfinite(rho_amb[a]) || !(rho_amb[a] > 0.f))
+            return fail(c, LBM_EINVAL, "rho_amb[%d] must be a positive number", a);
+        c->rho_amb[a] = rho_amb[a];
+    }
+
+    // per-block masks, ambient test, initial active set
+    const long long nb = c->nblocks;
+    c->solid_h.assign(nb * MASK_WORDS, 0u);
+    c->held_h.assign(nb * MASK_WORDS, 0u);
+    c->nonsolid_h.assign(nb, 0);
+    std::vector<char> differs(nb, 0);
+    for (int z = 0; z < p.nz; ++z)
+        for (int y = 0; y < p.ny; ++y)
+            for (int x = 0; x < p.nx; ++x) {
+                const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
+                const long long b = (x / EDGE) + c->nbx * ((long long)(y / EDGE) + (long long)c->nby * (z / EDGE));
+                const int lc = (x & 7) | ((y & 7) << 3) | ((z & 7) << 6);
+                if (cell_type[i] == LBM_CELL_SOLID) {
+                    c->solid_h[b * MASK_WORDS + (lc >> 5)] |= 1u << (lc & 31);
+                    continue;
+                }
+                if (cell_type[i] == LBM_CELL_HELD) c->held_h[b * MASK_WORDS + (lc >> 5)] |= 1u << (lc & 31);
+                c->nonsolid_h[b] += 1;
+                for (int a = 0; a < nc; ++a) {
+                    float r = rho_init[a * ncell + i];
+                    if (!std::isfinite(r) || !(r > 0.f))
+                        return fail(c, LBM_EINVAL, "rho_init[%d][%lld] must be a positive number", a, i);
+                    bool d = r != rho_amb[a];
+                    if (u_init)
+                        for (int k = 0; k < 3; ++k) d = d || u_init[(a * 3 + k) * ncell + i] != 0.f;
+                    if (d) differs[b] = 1;
+                }
+            }
+    std::vector<int> slot_of(nb, AMBIENT), block_of;
+    long long nonsolid_blocks = 0;
+    for (long long b = 0; b < nb; ++b) {
+        if (c->nonsolid_h[b] == 0) {
+            slot_of[b] = SOLIDBLK;
+            for (int w = 0; w < MASK_WORDS; ++w) c->solid_h[b * MASK_WORDS + w] = 0xffffffffu;
+            continue;
+        }
+        ++nonsolid_blocks;
+        if (!p.progressive || differs[b]) {
+            slot_of[b] = (int)block_of.size();
+            block_of.push_back((int)b);
+        }
+    }
+    const int n0 = (int)block_of.size();
+    if (n0 > c->capacity)
+        return fail(c, LBM_ENOMEM, "%d initial blocks exceed the pool capacity %d", n0, c->capacity);
+
+    KParams &k = c->kp;
+    for (int a = 0; a < 2; ++a) {
+        k.rho_amb[a] = a < nc ? rho_amb[a] : 0.f;
+        for (int i = 0; i < Q; ++i) k.famb[a][i] = weight_f(i) * k.rho_amb[a];
+    }
+    cudaStream_t s = c->stream;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(k.slot_of, slot_of.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (n0)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(k.block_of, block_of.data(), n0 * sizeof(int), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.solid, c->solid_h.data(), nb * MASK_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.held, c->held_h.data(), nb * MASK_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(k.cand_mark, 0, nb * sizeof(unsigned), s));
+    Ctrl ctrl{};
+    ctrl.n_active[0] = ctrl.n_active[1] = n0;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(k.ctrl, &ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    CUDA_OR_FAIL(c, launch_ambient_psi(k, s));
+    float psi_amb = 0.f;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(&psi_amb, &k.ctrl->psi_amb, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    k.psi_amb = psi_amb;
+
+    // initial populations, staged block-major in chunks
+    const int per_chunk = (int)(c->stage_floats / ((size_t)nc * 4 * CELLS));
+    std::vector<float> host((size_t)per_chunk * nc * 4 * CELLS);
+    for (int s0 = 0; s0 < n0; s0 += per_chunk) {
+        const int m = std::min(per_chunk, n0 - s0);
+        for (int r = 0; r < m; ++r) {
+            const int b = block_of[s0 + r];
+            const int bx = b % c->nbx, by = (b / c->nbx) % c->nby, bz = b / (c->nbx * c->nby);
+            for (int a = 0; a < nc; ++a) {
+                float *dst = host.data() + ((size_t)r * nc + a) * 4 * CELLS;
+                for (int lc = 0; lc < CELLS; ++lc) {
+                    const int x = bx * EDGE + (lc & 7), y = by * EDGE + ((lc >> 3) & 7),
+                              z = bz * EDGE + (lc >> 6);
+                    const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
+                    dst[lc] = rho_init[a * ncell + i];
+                    for (int d = 0; d < 3; ++d)
+                        dst[(d + 1) * CELLS + lc] = u_init ? u_init[(a * 3 + d) * ncell + i] : 0.f;
+                }
+            }
+        }
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(c->stage, host.data(), (size_t)m * nc * 4 * CELLS * sizeof(float),
+                                        cudaMemcpyHostToDevice, s));
+        CUDA_OR_FAIL(c, launch_init(k, c->stage, s0, m, std::min(m, persistent_grid(c)), s));
+        c->launches += 1;
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    }
+    c->slot_of_h = slot_of;
+    c->step = 0;
+    c->sticky = LBM_OK;
+    c->geometry = true;
+    return LBM_OK;
+}
+
+int lbm_step_async(lbm_ctx *c, int nsteps)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
+    if (c->sticky) return fail(c, LBM_ESTATE, "stepping refused after an earlier error (%d)", c->sticky);
+    if (nsteps < 0) return fail(c, LBM_EINVAL, "nsteps must be >= 0");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(c, LBM_ECUDA, "cannot select device %d", c->device);
+    return enqueue_steps(c, nsteps);
+}
+
+int lbm_sync(lbm_ctx *c)
+{
+    if (!c) return LBM_EINVAL;
+    DeviceGuard g(c->device);
+    return finish(c);
+}
+
+int lbm_step(lbm_ctx *c, int nsteps)
+{
+    int rc = lbm_step_async(c, nsteps);
+    if (rc) return rc;
+    return lbm_sync(c);
+}
+
+int lbm_get_macro(lbm_ctx *c, int comp, float *rho, float *ux, float *uy, float *uz)
+{
+    if (!c) return LBM_EINVAL;
+    if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
+    if (comp < 0 || comp >= c->p.ncomp) return fail(c, LBM_EINVAL, "comp %d out of range", comp);
+    DeviceGuard g(c->device);
+    const lbm_params &p = c->p;
+    const long long ncell = (long long)p.nx * p.ny * p.nz;
+    float *outs[4] = {rho, ux, uy, uz};
+    // unmeshed and solid cells first
+    for (long long b = 0; b < c->nblocks; ++b) {
+        const int bx = (int)(b % c->nbx), by = (int)((b / c->nbx) % c->nby),
+                  bz = (int)(b / ((long long)c->nbx * c->nby));
+        for (int lc = 0; lc < CELLS; ++lc) {
+            const int x = bx * EDGE + (lc & 7), y = by * EDGE + ((lc >> 3) & 7), z = bz * EDGE + (lc >> 6);
+            const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
+            const bool sol = (c->solid_h[b * MASK_WORDS + (lc >> 5)] >> (lc & 31)) & 1u;
+            if (rho) rho[i] = sol ? 0.f : c->rho_amb[comp];
+            for (int m = 1; m < 4; ++m)
+                if (outs[m]) outs[m][i] = 0.f;
+        }
+    }
+    (void)ncell;
+    Ctrl ctrl;
+    int rc = read_ctrl(c, ctrl);
+    if (rc) return rc;
+    const int n = ctrl.n_active[c->step & 1];
+    if (n == 0) return LBM_OK;
+    std::vector<int> block_of(n);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(block_of.data(), c->kp.block_of, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    const int rd = (int)(c->step & 1);
+    const int grid = persistent_grid(c);
+    CUDA_OR_FAIL(c, launch_macro(c->kp, (int)c->step, 0, grid, c->stream));
+    c->launches += 1;
+    const int per_chunk = (int)(c->stage_floats / (4 * CELLS));
+    std::vector<float> host((size_t)per_chunk * 4 * CELLS);
+    for (int s0 = 0; s0 < n; s0 += per_chunk) {
+        const int m = std::min(per_chunk, n - s0);
+        CUDA_OR_FAIL(c, launch_output(c->kp, rd, comp, s0, m, c->stage, std::min(m, grid), c->stream));
+        c->launches += 1;
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(host.data(), c->stage, (size_t)m * 4 * CELLS * sizeof(float),
+                                        cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+        for (int r = 0; r < m; ++r) {
+            const int b = block_of[s0 + r];
+            const int bx = b % c->nbx, by = (b / c->nbx) % c->nby, bz = b / (c->nbx * c->nby);
+            for (int lc = 0; lc < CELLS; ++lc) {
+                const int x = bx * EDGE + (lc & 7), y = by * EDGE + ((lc >> 3) & 7), z = bz * EDGE + (lc >> 6);
+                const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
+                for (int q = 0; q < 4; ++q)
+                    if (outs[q]) outs[q][i] = host[((size_t)r * 4 + q) * CELLS + lc];
+            }
+        }
+    }
+    return LBM_OK;
+}
+
+int lbm_active_blocks(lbm_ctx *c, int32_t *ids, long long cap, long long *n)
+{
+    if (!c || !n) return LBM_EINVAL;
+    if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
+    if (cap > 0 && !ids) return fail(c, LBM_EINVAL, "ids is NULL");
+    DeviceGuard g(c->device);
+    int na = 0;
+    int rc = active_count(c, &na);
+    if (rc) return rc;
+    std::vector<int32_t> all(na);
+    if (na) {
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(all.data(), c->kp.block_of, na * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    }
+    std::sort(all.begin(), all.end());
+    *n = na;
+    for (long long i = 0; i < std::min<long long>(cap, na); ++i) ids[i] = all[i];
+    return LBM_OK;
+}
+
+int lbm_mass(lbm_ctx *c, double *mass)
+{
+    if (!c || !mass) return LBM_EINVAL;
+    if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
+    DeviceGuard g(c->device);
+    int na = 0;
+    int rc = active_count(c, &na);
+    if (rc) return rc;
+    std::vector<int32_t> act(na);
+    if (na)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(act.data(), c->kp.block_of, na * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    const int rd = (int)(c->step & 1);
+    CUDA_OR_FAIL(c, launch_mass(c->kp, rd, na, c->mass_partial, c->mass_out,
+                                std::max(1, std::min(na, persistent_grid(c))), c->stream));
+    c->launches += na > 0 ? 2 : 1;
+    double dev[2] = {0, 0};
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(dev, c->mass_out, sizeof dev, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    std::vector<char> meshed(c->nblocks, 0);
+    for (int b : act) meshed[b] = 1;
+    long long amb_cells = 0;
+    for (long long b = 0; b < c->nblocks; ++b)
+        if (!meshed[b]) amb_cells += c->nonsolid_h[b];
+    for (int a = 0; a < c->p.ncomp; ++a) {
+        double per = 0.0;
+        for (int i = 0; i < Q; ++i) per += (double)c->kp.famb[a][i];
+        mass[a] = dev[a] + per * (double)amb_cells;
+    }
+    return LBM_OK;
+}
+
+int lbm_get_block_populations(lbm_ctx *c, int32_t block_id, float *out)
+{
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
+    if (block_id < 0 || block_id >= c->nblocks) return fail(c, LBM_EINVAL, "block %d out of range", block_id);
+    DeviceGuard g(c->device);
+    int slot = -1;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(&slot, c->kp.slot_of + block_id, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    if (slot < 0) return fail(c, LBM_EINVAL, "block %d is not meshed", block_id);
+    const float *src = c->kp.f + (size_t)(c->step & 1) * c->kp.buf_stride + (size_t)slot * c->kp.slot_floats;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(out, src, (size_t)c->kp.slot_floats * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_velocities(int32_t *e)
+{
+    if (!e) return LBM_EINVAL;
+    for (int i = 0; i < Q; ++i)
+        for (int d = 0; d < 3; ++d) e[3 * i + d] = EV[i][d];
+    return LBM_OK;
+}
+
+int lbm_set_profiling(lbm_ctx *c, int on)
+{
+    if (!c) return LBM_EINVAL;
+    c->profiling = on != 0;
+    return LBM_OK;
+}
+
+int lbm_get_stats(lbm_ctx *c, lbm_stats *out)
+{
+    if (!c || !out) return LBM_EINVAL;
+    DeviceGuard g(c->device);
+    std::memset(out, 0, sizeof *out);
+    out->capacity = c->capacity;
+    out->total_blocks = c->nblocks;
+    out->launches = c->launches;
+    out->device_bytes = c->device_bytes;
+    out->steps = c->step;
+    if (c->geometry) {
+        Ctrl ctrl;
+        int rc = read_ctrl(c, ctrl);
+        if (rc) return rc;
+        flush_profile(c);
+        out->active_blocks = ctrl.n_active[c->step & 1];
+        out->cell_updates = (long long)ctrl.cell_updates;
+        long long ns = 0;
+        for (int v : c->nonsolid_h) ns += v > 0;
+        out->nonsolid_blocks = ns;
+    }
+    for (int k = 0; k < 4; ++k) {
+        out->kernel_ms[k] = c->kernel_ms[k];
+        out->kernel_launches[k] = c->kernel_launches[k];
+    }
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err : g_create_error; }
+
+}  // extern "C"

@@ -1,0 +1,86 @@
+// Internal types shared by the host runtime (lbm_capi.cpp) and the kernels
+// (lbm_kernels.cu).  Not part of the public C ABI (include/lbm.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+constexpr int EDGE = 8;     // cells per block edge
+constexpr int CELLS = 512;  // cells per block
+constexpr int Q = 19;       // D3Q19
+constexpr int MACS = 3;     // per-cell scratch written by the stream pass: rho0, psi0, rho1
+constexpr int MASK_WORDS = CELLS / 32;
+
+// slot_of[] values besides a slot index
+constexpr int AMBIENT = -1;  // unmeshed block (at least one non-solid cell)
+constexpr int SOLIDBLK = -2; // every cell solid, or outside a non-periodic axis
+
+// Device-resident control words.  Counts are double-buffered by step
+// parity so that no kernel has to reset a word another kernel of the same
+// step still reads.
+struct Ctrl {
+    int n_active[2];   // meshed blocks at the start of a step of this parity
+    int ncand[2];      // candidate blocks found by the criterion
+    int status;        // 0, or an LBM_E* code raised on the device
+    int fail_step;     // step at which status was raised
+    unsigned long long cell_updates;
+    float psi_amb;     // psi of the ambient density, evaluated on the device
+    int pad;
+};
+
+// Everything a kernel needs, passed by value.
+struct KParams {
+    int nbx, nby, nbz;
+    int per[3];
+    int ncomp;
+    int capacity;
+    int progressive;
+    // physics, FP32
+    float omega;        // 1 / tau
+    float beta, g_self, g_cross;
+    float g_ads[2];
+    float grav[3];
+    float rho_ref[2];
+    float S2;           // S^2
+    float pr_b, pr_RT, pr_atheta;
+    float psi_scale;    // 2 / (c_s^2 g_self), 0 when g_self == 0
+    float rho_amb[2];
+    float psi_amb;
+    float famb[2][Q];   // ambient resting populations w_i rho_amb
+    // device memory
+    float *f;           // [2][capacity][ncomp][Q][CELLS]
+    float *mac;         // [capacity][MACS][CELLS]
+    float *uprev;       // [capacity][ncomp][3][CELLS]
+    int *slot_of;       // [nblocks]
+    int *block_of;      // [capacity]
+    const uint32_t *solid;  // [nblocks][MASK_WORDS]
+    const uint32_t *held;   // [nblocks][MASK_WORDS]
+    int *cand_list;     // [nblocks]
+    unsigned *cand_mark;    // [nblocks]
+    Ctrl *ctrl;
+    size_t buf_stride;  // floats per population buffer
+    int slot_floats;    // ncomp * Q * CELLS
+};
+
+// Kernel kinds for per-kernel timing.
+enum KernelKind { K_MACRO = 0, K_ACTIVATE = 1, K_COLLIDE = 2, K_OTHER = 3 };
+
+// Launch wrappers (lbm_kernels.cu).  All enqueue on `s` and return the
+// launch status.
+cudaError_t launch_init(const KParams &kp, const float *in_block, int slot0, int nslots,
+                        int grid, cudaStream_t s);
+cudaError_t launch_ambient_psi(const KParams &kp, cudaStream_t s);
+cudaError_t launch_macro(const KParams &kp, int step, int criterion, int grid, cudaStream_t s);
+cudaError_t launch_activate(const KParams &kp, int step, int grid, cudaStream_t s);
+cudaError_t launch_collide(const KParams &kp, int step, int grid, cudaStream_t s);
+cudaError_t launch_output(const KParams &kp, int rd, int comp, int slot0, int nslots, float *out,
+                          int grid, cudaStream_t s);
+cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, double *out, int grid,
+                        cudaStream_t s);
+int max_ctas_per_sm_stream_kernels();
+
+}  // namespace lbm

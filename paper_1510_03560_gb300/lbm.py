@@ -1,0 +1,280 @@
+"""ctypes binding of liblbm (include/lbm.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  PyTorch
+provides the device memory (its caching allocator, through the library's
+allocator callbacks) and the CUDA stream.  There is no fallback: if the
+library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, 1, 2, 3, 4
+Q = 19
+EDGE = 8
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("ncomp", C.c_int),
+        ("periodic", C.c_int * 3),
+        ("progressive", C.c_int),
+        ("tau", C.c_double), ("beta", C.c_double),
+        ("pr_a", C.c_double), ("pr_b", C.c_double), ("pr_R", C.c_double), ("pr_omega", C.c_double),
+        ("T_over_Tc", C.c_double),
+        ("g_self", C.c_double), ("g_cross", C.c_double),
+        ("g_ads", C.c_double * 2),
+        ("grav", C.c_double * 3),
+        ("rho_ref", C.c_double * 2),
+        ("S", C.c_double),
+        ("max_blocks", C.c_longlong),
+        ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", C.c_void_p),
+        ("stream", C.c_void_p),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_longlong), ("active_blocks", C.c_longlong), ("capacity", C.c_longlong),
+        ("total_blocks", C.c_longlong), ("nonsolid_blocks", C.c_longlong),
+        ("cell_updates", C.c_longlong), ("launches", C.c_longlong), ("device_bytes", C.c_longlong),
+        ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_longlong * 4),
+    ]
+
+
+EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_step", "lbm_step_async",
+           "lbm_sync", "lbm_get_macro", "lbm_active_blocks", "lbm_mass",
+           "lbm_get_block_populations", "lbm_velocities", "lbm_set_profiling", "lbm_get_stats",
+           "lbm_last_error"]
+
+_lib = None
+
+
+class LBMError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblbm error {code}: {msg}")
+        self.code = code
+
+
+def load():
+    """Load liblbm.so (built by paper_1510_03560_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1510_03560_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, ip, fp, dp, u8p = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_float), \
+        C.POINTER(C.c_double), C.POINTER(C.c_uint8)
+    lib.lbm_create.argtypes = [C.POINTER(Params), C.POINTER(vp)]
+    lib.lbm_destroy.argtypes = [vp]
+    lib.lbm_set_geometry.argtypes = [vp, u8p, fp, fp, fp]
+    lib.lbm_step.argtypes = [vp, C.c_int]
+    lib.lbm_step_async.argtypes = [vp, C.c_int]
+    lib.lbm_sync.argtypes = [vp]
+    lib.lbm_get_macro.argtypes = [vp, C.c_int, fp, fp, fp, fp]
+    lib.lbm_active_blocks.argtypes = [vp, ip, C.c_longlong, C.POINTER(C.c_longlong)]
+    lib.lbm_mass.argtypes = [vp, dp]
+    lib.lbm_get_block_populations.argtypes = [vp, C.c_int32, fp]
+    lib.lbm_velocities.argtypes = [ip]
+    lib.lbm_set_profiling.argtypes = [vp, C.c_int]
+    lib.lbm_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    lib.lbm_last_error.argtypes = [vp]
+    lib.lbm_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        if name != "lbm_last_error":
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def velocities() -> np.ndarray:
+    e = np.zeros((Q, 3), dtype=np.int32)
+    load().lbm_velocities(e.ctypes.data_as(C.POINTER(C.c_int32)))
+    return e
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+class _TorchAllocator:
+    """Allocator callbacks backed by torch's CUDA caching allocator."""
+
+    def __init__(self, torch, device, stream):
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+
+        def alloc(nbytes, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:
+                return None
+
+        def free(ptr, user):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        self.alloc = ALLOC_FN(alloc)
+        self.free = FREE_FN(free)
+
+
+class LBM:
+    """One simulation context (lbm_ctx).
+
+    Keyword parameters mirror lbm_params: nx, ny, nz, ncomp, periodic,
+    progressive, tau, beta, pr_a, pr_b, pr_R, pr_omega, T_over_Tc, g_self,
+    g_cross, g_ads, grav, rho_ref, S, max_blocks.  ``stream``: a
+    torch.cuda.Stream (default: the current stream).  ``torch_alloc``:
+    allocate through torch's caching allocator (default) or let the library
+    use cudaMallocAsync.
+    """
+
+    def __init__(self, stream=None, torch_alloc=True, **kw):
+        import torch
+        self.lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblbm needs a CUDA GPU")
+        self.device = torch.cuda.current_device()
+        self.torch_stream = stream if stream is not None else torch.cuda.current_stream()
+        p = Params()
+        p.nx, p.ny, p.nz = int(kw["nx"]), int(kw["ny"]), int(kw["nz"])
+        self.shape = (p.nz, p.ny, p.nx)
+        p.ncomp = int(kw.get("ncomp", 2))
+        self.ncomp = p.ncomp
+        per = kw.get("periodic", (1, 1, 0))
+        for a in range(3):
+            p.periodic[a] = int(per[a])
+        p.progressive = int(kw.get("progressive", 1))
+        p.tau = float(kw.get("tau", 1.0))
+        p.beta = float(kw.get("beta", 1.16))
+        p.pr_a = float(kw.get("pr_a", 2.0 / 49.0))
+        p.pr_b = float(kw.get("pr_b", 2.0 / 21.0))
+        p.pr_R = float(kw.get("pr_R", 1.0))
+        p.pr_omega = float(kw.get("pr_omega", 0.344))
+        p.T_over_Tc = float(kw.get("T_over_Tc", 0.85))
+        p.g_self = float(kw.get("g_self", -1.0))
+        p.g_cross = float(kw.get("g_cross", 0.0))
+        ga = kw.get("g_ads", (0.0, 0.0))
+        p.g_ads[0], p.g_ads[1] = float(ga[0]), float(ga[1])
+        g = kw.get("grav", (0.0, 0.0, 0.0))
+        for d in range(3):
+            p.grav[d] = float(g[d])
+        rr = kw.get("rho_ref", (0.0, 0.0))
+        p.rho_ref[0] = float(rr[0])
+        p.rho_ref[1] = float(rr[1]) if len(rr) > 1 else 0.0
+        p.S = float(kw.get("S", 0.0))
+        p.max_blocks = int(kw.get("max_blocks", 0))
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = _TorchAllocator(torch, self.device, self.torch_stream.cuda_stream)
+            p.dev_alloc = self._alloc.alloc
+            p.dev_free = self._alloc.free
+        p.stream = self.torch_stream.cuda_stream
+        self.params = p
+        h = C.c_void_p()
+        rc = self.lib.lbm_create(C.byref(p), C.byref(h))
+        if rc != OK:
+            raise LBMError(rc, self.lib.lbm_last_error(None).decode())
+        self.h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LBMError(rc, self.lib.lbm_last_error(self.h).decode())
+
+    # -- API
+    def set_geometry(self, cell_type, rho_init, u_init, rho_amb):
+        ct = np.ascontiguousarray(cell_type, dtype=np.uint8)
+        assert ct.shape == self.shape
+        self._keep = (ct, _f32(rho_init), None if u_init is None else _f32(u_init), _f32(rho_amb))
+        ct, ri, ui, ra = self._keep
+        self._check(self.lib.lbm_set_geometry(self.h, ct.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                              _fptr(ri), _fptr(ui), _fptr(ra)))
+
+    def step(self, n: int = 1):
+        self._check(self.lib.lbm_step(self.h, int(n)))
+
+    def step_async(self, n: int = 1):
+        self._check(self.lib.lbm_step_async(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.lib.lbm_sync(self.h))
+
+    def macro(self, comp: int):
+        out = [np.zeros(self.shape, dtype=np.float32) for _ in range(4)]
+        self._check(self.lib.lbm_get_macro(self.h, int(comp), *[_fptr(a) for a in out]))
+        return tuple(out)
+
+    def active_blocks(self) -> np.ndarray:
+        n = C.c_longlong()
+        self._check(self.lib.lbm_active_blocks(self.h, None, 0, C.byref(n)))
+        ids = np.zeros(max(n.value, 1), dtype=np.int32)
+        self._check(self.lib.lbm_active_blocks(self.h, ids.ctypes.data_as(C.POINTER(C.c_int32)),
+                                               n.value, C.byref(n)))
+        return ids[: n.value].copy()
+
+    def mass(self) -> np.ndarray:
+        m = np.zeros(2)
+        self._check(self.lib.lbm_mass(self.h, m.ctypes.data_as(C.POINTER(C.c_double))))
+        return m[: self.ncomp].copy()
+
+    def block_populations(self, block_id: int) -> np.ndarray:
+        out = np.zeros((self.ncomp, Q, 512), dtype=np.float32)
+        self._check(self.lib.lbm_get_block_populations(self.h, int(block_id), _fptr(out)))
+        return out
+
+    def set_profiling(self, on: bool):
+        self._check(self.lib.lbm_set_profiling(self.h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self.lib.lbm_get_stats(self.h, C.byref(s)))
+        d = {k: getattr(s, k) for k, _ in Stats._fields_ if k not in ("kernel_ms", "kernel_launches")}
+        d["kernel_ms"] = list(s.kernel_ms)
+        d["kernel_launches"] = list(s.kernel_launches)
+        return d
+
+
+def from_case(case, **over):
+    """Context + geometry from a workloads case dict."""
+    p = dict(case["params"])
+    p.pop("block", None)
+    p.update(over)
+    sim = LBM(**p)
+    sim.set_geometry(case["cell_type"], case["rho_init"], case["u_init"], case["rho_amb"])
+    return sim

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle
+on the same seeded inputs.  Tolerances: density 1e-4 relative, velocity
+1e-5 absolute, meshed-block sets identical at every step."""
+import numpy as np
+import pytest
+
+from gpu_helpers import (compare_fields, gpu_of, oracle_of, order_map, run_pair, block_cells)
+from oracle import oracle as O
+from paper_1510_03560_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    from paper_1510_03560_gb300 import build as B
+    B.build()
+    from paper_1510_03560_gb300 import lbm
+    assert torch.cuda.is_available()
+    return lbm
+
+
+def test_drop_in_box_progressive_200_steps(L):
+    """32^3 two-component drop, 8^3 blocks, periodic x/y, floor, gravity,
+    progressive mesh from the blocks holding the liquid, 200 steps."""
+    case = W.drop_in_box()
+    gpu, orc, counts = run_pair(L, case, 200)
+    assert counts[0] == 8 and counts[-1] > counts[0]
+    compare_fields(gpu, orc, case, label="drop 200")
+    np.testing.assert_allclose(gpu.mass(), orc.mass(), rtol=1e-6)
+
+
+def test_drop_in_box_static(L):
+    case = W.drop_in_box(progressive=0)
+    gpu, orc, counts = run_pair(L, case, 60)
+    assert counts[0] == 64
+    compare_fields(gpu, orc, case, label="static")
+    m0 = orc.mass()
+    np.testing.assert_allclose(gpu.mass(), m0, rtol=1e-6)
+
+
+@pytest.mark.parametrize("tau", [0.8, 1.3])
+def test_relaxation_time_other_than_one(L, tau):
+    case = W.drop_in_box(progressive=1)
+    gpu, orc, _ = run_pair(L, case, 60, tau=tau)
+    compare_fields(gpu, orc, case, label=f"tau {tau}")
+
+
+def test_porous_injection_ragged_grid(L):
+    """Non-cubic, non-periodic grid (7 x 5 x 6 blocks) with seeded spheres,
+    an inlet patch and an outlet face of held cells, wetting walls."""
+    case = W.porous_injection(n=(56, 40, 48), seed=1510035603, inlet=16, x_free=6,
+                              r_range=(3.0, 6.0), u_in=0.02, S=1e-4)
+    gpu, orc, counts = run_pair(L, case, 120)
+    assert counts[-1] > counts[0]
+    compare_fields(gpu, orc, case, label="porous")
+
+
+def test_single_component_droplet(L):
+    case = W.droplet(n=32, R=9.0, rho_vap=0.42)
+    gpu, orc, _ = run_pair(L, case, 100)
+    compare_fields(gpu, orc, case, label="droplet")
+    np.testing.assert_allclose(gpu.mass(), orc.mass(), rtol=1e-6)
+
+
+def test_single_component_channel_flow(L):
+    case = W.channel(H=14, nxy=8, gx=1e-5)
+    gpu, orc, _ = run_pair(L, case, 200, check_active=False)
+    compare_fields(gpu, orc, case, label="channel")
+
+
+def test_empty_mesh_stays_ambient(L):
+    """Everything at the ambient state: nothing is meshed, nothing moves."""
+    case = W.drop_in_box()
+    case["rho_init"][0] = np.float32(W.RHO_VAP)
+    case["rho_init"][1] = 1.0
+    gpu, orc, counts = run_pair(L, case, 5)
+    assert counts == [0] * 6
+    r, ux, uy, uz = gpu.macro(0)
+    fluid = case["cell_type"] == 0
+    assert np.all(r[fluid] == np.float32(W.RHO_VAP)) and not ux.any() and not uz.any()
+    np.testing.assert_allclose(gpu.mass(), orc.mass(), rtol=1e-6)
+
+
+def test_fully_solid_blocks_never_mesh(L):
+    case = W.drop_in_box()
+    case["cell_type"][:, :8, :8] = 1  # a solid column of blocks
+    gpu, orc, counts = run_pair(L, case, 40)
+    nbx = 4
+    solid_blocks = [bx + nbx * (0 + nbx * bz) for bz in range(4) for bx in range(1)]
+    assert not set(solid_blocks) & set(gpu.active_blocks().tolist())
+    compare_fields(gpu, orc, case, label="solid blocks")
+
+
+def test_pool_exhaustion_keeps_last_complete_step(L):
+    """A pool too small for the blocks a step creates: LBM_ENOMEM, state left
+    at the last completed step, further steps refused."""
+    case = W.drop_in_box()
+    small = gpu_of(L, case, max_blocks=12)
+    ref = gpu_of(L, case)
+    failed_at = None
+    for t in range(40):
+        try:
+            small.step(1)
+        except L.LBMError as e:
+            assert e.code == L.ENOMEM
+            failed_at = t
+            break
+        ref.step(1)
+    assert failed_at is not None
+    assert small.stats()["steps"] == failed_at
+    for a in range(2):
+        for x, y in zip(small.macro(a), ref.macro(a)):
+            np.testing.assert_array_equal(x, y)
+    with pytest.raises(L.LBMError):
+        small.step(1)
+
+
+def test_async_steps_match_synchronous(L):
+    case = W.drop_in_box()
+    a = gpu_of(L, case)
+    b = gpu_of(L, case)
+    a.step(30)
+    for _ in range(3):
+        b.step_async(10)
+    b.sync()
+    np.testing.assert_array_equal(a.active_blocks(), b.active_blocks())
+    for x, y in zip(a.macro(0), b.macro(0)):
+        np.testing.assert_array_equal(x, y)
+    st = b.stats()
+    assert st["steps"] == 30 and st["cell_updates"] > 0
+
+
+def one_step_sample(L, gpu, case, block_ids):
+    """For each sampled block whose 26 neighbours are all meshed: rebuild its
+    3 x 3 x 3-block neighbourhood in the oracle from the library's current
+    populations, advance one step on both, compare the centre block."""
+    nx, ny, nz = (case["params"][k] for k in ("nx", "ny", "nz"))
+    omap = order_map(L)
+    before = {}
+    for b in block_ids:
+        x0, y0, z0 = block_cells(nx, ny, nz, b)
+        sub = {}
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    bx, by, bz = x0 // 8 + dx, y0 // 8 + dy, z0 // 8 + dz
+                    nb = bx + (nx // 8) * (by + (ny // 8) * bz)
+                    sub[(dx, dy, dz)] = gpu.block_populations(nb)
+        before[b] = sub
+    gpu.step(1)
+    for b in block_ids:
+        x0, y0, z0 = block_cells(nx, ny, nz, b)
+        ct = case["cell_type"][z0 - 8:z0 + 16, y0 - 8:y0 + 16, x0 - 8:x0 + 16]
+        ncomp = case["params"]["ncomp"]
+        rho = np.ones((ncomp,) + ct.shape)
+        p = dict(case["params"], nx=24, ny=24, nz=24, progressive=0, periodic=(0, 0, 0))
+        orc = O.OracleSim(ct, rho, None, case["rho_amb"].astype(np.float64), **p)
+        for a in range(ncomp):
+            f = np.zeros((24, 24, 24, 19))
+            for (dx, dy, dz), pops in before[b].items():
+                blk = pops[a].reshape(19, 8, 8, 8)  # [dir][z][y][x]
+                f[(dz + 1) * 8:(dz + 2) * 8, (dy + 1) * 8:(dy + 2) * 8,
+                  (dx + 1) * 8:(dx + 2) * 8, :][..., omap] = np.moveaxis(blk, 0, -1)
+            orc.set_f(a, f)
+        orc.step(1)
+        after = gpu.block_populations(b)
+        for a in range(ncomp):
+            want = orc.get_f(a)[8:16, 8:16, 8:16][..., omap]  # [z][y][x][dir]
+            got = np.moveaxis(after[a].reshape(19, 8, 8, 8), 0, -1)
+            cells = ct[8:16, 8:16, 8:16] == 0
+            np.testing.assert_allclose(got[cells], want[cells], rtol=2e-5,
+                                       atol=2e-6 * np.abs(want[cells]).max())
+
+
+def interior_meshed_blocks(gpu, case, count, seed=0):
+    nx, ny, nz = (case["params"][k] for k in ("nx", "ny", "nz"))
+    nbx, nby, nbz = nx // 8, ny // 8, nz // 8
+    act = set(gpu.active_blocks().tolist())
+    rng = np.random.default_rng(seed)
+    picks = []
+    for b in rng.permutation(sorted(act)):
+        bx, by, bz = b % nbx, (b // nbx) % nby, b // (nbx * nby)
+        if not (0 < bx < nbx - 1 and 0 < by < nby - 1 and 0 < bz < nbz - 1):
+            continue
+        nbs = [(bx + dx) + nbx * ((by + dy) + nby * (bz + dz))
+               for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+        if all(n in act for n in nbs):
+            picks.append(int(b))
+        if len(picks) == count:
+            break
+    return picks
+
+
+def test_full_size_injection_sampled_one_step(L):
+    """256^3 porous injection in the benchmark's launch configuration: after
+    300 steps, one further step of sampled interior blocks equals the
+    oracle's step from the same populations; the meshed set stays connected."""
+    case = W.porous_injection()
+    gpu = gpu_of(L, case)
+    gpu.step(300)
+    picks = interior_meshed_blocks(gpu, case, 4)
+    assert len(picks) >= 2
+    one_step_sample(L, gpu, case, picks)
+    act = set(gpu.active_blocks().tolist())
+    nbx = nby = 32
+    for b in act:
+        bx, by, bz = b % nbx, (b // nbx) % nby, b // (nbx * nby)
+        nbs = [(bx + dx) + nbx * ((by + dy) + nby * (bz + dz))
+               for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+               if (dx, dy, dz) != (0, 0, 0) and abs(dx) + abs(dy) + abs(dz) <= 2]
+        assert any(n in act for n in nbs)
