@@ -1,0 +1,369 @@
+"""Benchmark: active-cell MLUPS and fraction of the HBM roofline of the
+progressive-mesh two-component LBM step, against the static mesh, on one
+GB300 (replicas on N GPUs under torchrun).
+
+Workload: 256^3 liquid injection into a gas-filled porous box (seeded
+spheres, radius 6-12, solid fraction 0.30, 64^2 inlet at u = 0.02, wetting
+g_ads = -0.2, Peng-Robinson component + ideal-gas component), 5000 time
+steps in total: W untimed warm-up steps from the initial state, then K timed
+steps.  A "step" is one time step of the whole hot path (streaming,
+moments, criterion and block creation, forces, collision).
+
+Timing: every timed step is bracketed by CUDA events on the library's
+stream; before each one a 256 MiB buffer is written to flush the 129 MB
+L2, outside the events.  MLUPS counts 512 cells for every meshed block of
+every timed step (Eq. 16 with the meshed cells as the domain).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "active-cell MLUPS (D3Q19, 2 comp) & % HBM roofline vs static mesh, same GPU"
+BYTES_PER_UPDATE = 304  # FP32: 2 components x 19 populations x 4 B, read + write
+WORKLOAD = ("porous injection 256^3 (seeded spheres r 6-12, solid 0.30, 64^2 inlet u=0.02, "
+            "g_ads=-0.2, 2 components), 5000 steps, 8^3 blocks")
+CPU_SAMPLE = "64^3 crop of the same recipe (seed 1510035603, 16^2 inlet), progressive mesh"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """ncu DRAM bytes per meshed cell of the force+collide kernel, if the
+    committed capture was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1510_03560_gb300", "csrc", "lbm_kernels.cu")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("kernels_sha256") == h:
+            return float(d["collide_dram_bytes_per_cell"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.uuid = device_uuid
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def device_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def make_case(S=None):
+    from paper_1510_03560_gb300 import workloads as W
+    kw = {} if S is None else {"S": S}
+    return W.porous_injection(**kw)
+
+
+def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid):
+    """Warm up, then time `steps` steps one by one (L2 flushed before each)."""
+    sim = L.from_case(case, progressive=progressive)
+    sim.step(warmup)
+    stream = torch.cuda.current_stream()
+    st0 = sim.stats()
+    sim.set_profiling(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record(stream)
+            sim.step_async(1)
+            ends[k].record(stream)
+        sim.sync()
+        torch.cuda.synchronize()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    st1 = sim.stats()
+    sim.set_profiling(False)
+    out = dict(
+        ms=ms,
+        cells=st1["cell_updates"] - st0["cell_updates"],
+        launches=st1["launches"] - st0["launches"],
+        kernel_ms=[b - a for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
+        kernel_launches=[b - a for a, b in zip(st0["kernel_launches"], st1["kernel_launches"])],
+        active_end=st1["active_blocks"],
+        nonsolid_blocks=st1["nonsolid_blocks"],
+        total_blocks=st1["total_blocks"],
+        clocks=clk.summary(),
+    )
+    sim.close()
+    return out
+
+
+def run_e2e(L, torch, case, steps):
+    """End to end through the public API with host buffers: geometry and
+    initial state uploaded, `steps` steps, both components' fields read
+    back; wall clock around all of it."""
+    import numpy as np
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim = L.from_case(case)
+    sim.step(steps)
+    outs = [sim.macro(a) for a in range(2)]
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = sim.stats()
+    sim.close()
+    h2d = case["cell_type"].nbytes + case["rho_init"].nbytes + case["u_init"].nbytes + 8
+    d2h = sum(a.nbytes for o in outs for a in o)
+    return dict(wall=wall, cells=st["cell_updates"], h2d=h2d, d2h=d2h, steps=steps,
+                checksum=float(np.float64(outs[0][0].sum())))
+
+
+def oracle_sample(budget_s=15.0, max_steps=None):
+    """The FP64 oracle on a bounded sample of the workload: active-cell MLUPS."""
+    from oracle import oracle as O
+    from paper_1510_03560_gb300 import workloads as W
+    case = W.porous_injection(n=(64, 64, 64), seed=1510035603, inlet=16, x_free=4)
+    p = dict(case["params"])
+    sim = O.OracleSim(case["cell_type"], case["rho_init"], case["u_init"], case["rho_amb"], **p)
+    cells, steps, t_used = 0, 0, 0.0
+    while t_used < budget_s and (max_steps is None or steps < max_steps):
+        t0 = time.perf_counter()
+        sim.step(1)
+        t_used += time.perf_counter() - t0
+        cells += 512 * len(sim.active_blocks())
+        steps += 1
+    sim.close()
+    return dict(mlups=cells / t_used / 1e6, steps=steps, seconds=t_used, cores=O.threads())
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    backend = "nccl"
+    dist.init_process_group(backend=backend)
+    return dist, dist.get_rank(), ws
+
+
+def reduce_max_sum(dist, torch, vmax, vsum):
+    if dist is None:
+        return vmax, vsum
+    t = torch.tensor([vmax], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([vsum], dtype=torch.float64, device="cuda")
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(s.item())
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    # each "step" a bounded sample: a few oracle steps of the 64^3 crop
+    per_step = 2
+    total_steps = args.warmup + args.steps
+    budget = max(20.0, min(150.0, 1.0 * total_steps))
+    r = oracle_sample(budget_s=budget, max_steps=per_step * total_steps)
+    line = {
+        "metric": METRIC, "value": round(r["mlups"], 4), "unit": "MLUPS", "impl": "reference",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * r["seconds"] / max(r["steps"], 1), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": CPU_SAMPLE, "oracle_steps": r["steps"]},
+        "cpu_baseline": {"value": round(r["mlups"], 4), "unit": "MLUPS", "cores": r["cores"],
+                         "kind": "oracle",
+                         "sample": f"{CPU_SAMPLE}, {r['steps']} steps, {r['seconds']:.1f} s"},
+        "e2e": {"value": round(r["mlups"], 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4950)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--S", type=float, default=None, help="criterion threshold override")
+    ap.add_argument("--no-static", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    import torch
+    dist, rank, world = dist_setup()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_1510_03560_gb300 import build as B
+    if rank == 0 or dist is None:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1510_03560_gb300 import lbm as L
+    uuid = device_uuid(torch, local)
+    case = make_case(args.S)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_max, cells_sum = reduce_max_sum(dist, torch, prog["ms"], prog["cells"])
+
+    stat = None
+    if not args.no_static:
+        stat = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid)
+        s_max, s_cells = reduce_max_sum(dist, torch, stat["ms"], stat["cells"])
+    e2e = None if args.no_e2e else run_e2e(L, torch, case, args.warmup + args.steps)
+    if e2e is not None:
+        e_max, e_cells = reduce_max_sum(dist, torch, e2e["wall"], e2e["cells"])
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = peaks()
+    mlups = cells_sum / (t_max * 1e-3) / 1e6
+    step_frac = prog["cells"] * BYTES_PER_UPDATE / (prog["ms"] * 1e-3) / 1e9 / peak
+    # dominant kernel: force + collide (kind 2); algorithmic bytes per launch =
+    # 304 B x meshed cells of that launch
+    kms, kn = prog["kernel_ms"][2], prog["kernel_launches"][2]
+    coll_gbs = prog["cells"] * BYTES_PER_UPDATE / (kms * 1e-3) / 1e9 if kms > 0 else None
+    traffic_pc = kernel_traffic()
+    avg_cells = prog["cells"] / max(kn, 1)
+    roofline = {
+        "bound": "hbm", "achieved": round(coll_gbs, 1) if coll_gbs else None,
+        "peak": peak, "unit": "GB/s",
+        "frac": round(coll_gbs / peak, 4) if coll_gbs else None,
+        "traffic": round(traffic_pc * avg_cells) if traffic_pc else None,
+        "kernel": "k_collide (force gather + exact-difference collision + pull streaming)",
+        "peak_kind": peak_kind,
+        "algorithmic_bytes_per_launch": round(avg_cells * BYTES_PER_UPDATE),
+        "avg_launch_ms": round(kms / max(kn, 1), 5),
+    }
+    share = {name: round(v / max(sum(prog["kernel_ms"]), 1e-9), 4)
+             for name, v in zip(("macro", "activate", "collide", "other"), prog["kernel_ms"])}
+    config = {
+        "workload": WORKLOAD, "mode": "progressive", "grid": [256, 256, 256], "block": [8, 8, 8],
+        "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
+        "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
+        "mean_active_fraction": round(prog["cells"] / 512 / args.steps / prog["total_blocks"], 4),
+        "step_hbm_frac": round(step_frac, 4), "kernel_time_share": share,
+        "l2": "256 MiB buffer written before every timed step; flush outside the timed events",
+        "parallelism": f"replicas x{world}",
+    }
+    if stat is not None:
+        s_mlups = s_cells / (s_max * 1e-3) / 1e6
+        config["static_mlups"] = round(s_mlups, 1)
+        config["static_step_hbm_frac"] = round(
+            stat["cells"] * BYTES_PER_UPDATE / (stat["ms"] * 1e-3) / 1e9 / peak, 4)
+        config["progressive_over_static_time"] = round(prog["ms"] / stat["ms"], 4)
+    cpu = None
+    if not args.no_cpu:
+        r = oracle_sample(budget_s=15.0)
+        cpu = {"value": round(r["mlups"], 4), "unit": "MLUPS", "cores": r["cores"],
+               "kind": "oracle",
+               "sample": f"{CPU_SAMPLE}, {r['steps']} steps, {r['seconds']:.1f} s"}
+    line = {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config, "roofline": roofline, "cpu_baseline": cpu,
+        "clocks": prog["clocks"],
+        "gpu_launches": prog["launches"],
+    }
+    if e2e is not None:
+        line["e2e"] = {"value": round(e_cells / e_max / 1e6, 1), "unit": "MLUPS",
+                       "h2d_bytes_per_step": round(e2e["h2d"] / e2e["steps"], 1),
+                       "d2h_bytes_per_step": round(e2e["d2h"] / e2e["steps"], 1)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -24,6 +24,7 @@ constexpr int EV[Q][3] = {
     {1, -1, 0},  {-1, 1, 0},  {0, 0, 1},  {1, 0, 1},  {-1, 0, 1}, {0, 1, 1},  {0, -1, 1},
     {0, 0, -1},  {-1, 0, -1}, {1, 0, -1}, {0, -1, -1}, {0, 1, -1}};
 
+// The kernels' FP32 weights.
 float weight_f(int i)
 {
     int n2 = EV[i][0] * EV[i][0] + EV[i][1] * EV[i][1] + EV[i][2] * EV[i][2];

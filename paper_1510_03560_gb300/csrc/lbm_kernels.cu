@@ -527,15 +527,24 @@ __global__ void __launch_bounds__(CELLS) k_collide(KParams kp, int step)
                 const float uu = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
                 float *dst = wr + (size_t)slot * kp.slot_floats + a * Q * CELLS + c;
                 const float r = rho[a];
-                Unroll<0, Q>::run([&]<int I>() {
+                // The 18 moving populations from Eqs. 10-12; the rest
+                // population from the mass balance sum_i f_i = rho, which
+                // the collision satisfies exactly in real arithmetic.  In
+                // FP32 this keeps the mass free of the systematic bias of
+                // the rounded weights (fl(1/3) + 6 fl(1/18) + 12 fl(1/36)
+                // = 1 + 1.5e-8).
+                float moving = 0.f;
+                Unroll<1, Q>::run([&]<int I>() {
                     const float wr_ = wgt(I) * r;
                     float v = feq<I>(wr_, vx, vy, vz, vv);
                     if (!TAU1) {
                         const float e0 = feq<I>(wr_, u[a][0], u[a][1], u[a][2], uu);
                         v += (1.f - kp.omega) * (fin[a][I] - e0);
                     }
+                    moving += v;
                     dst[I * CELLS] = v;
                 });
+                dst[0] = r - moving;
             }
             if (kp.progressive && (reach & nb.amb_bits)) {
 #pragma unroll

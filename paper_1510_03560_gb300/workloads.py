@@ -107,15 +107,19 @@ def spheres_mask(shape, seed, solid_frac, r_range, x_free):
 
 def porous_injection(n=(256, 256, 256), seed=1510035601, solid_frac=0.30, r_range=(6.0, 12.0),
                      inlet=64, u_in=0.02, g_ads=-0.2, x_free=16, S=2e-3, progressive=1,
-                     block=(8, 8, 8)):
+                     block=(8, 8, 8), rho_gas_in=0.1):
     """Liquid injected through an inlet patch into a gas-filled porous box.
 
     Grid nx*ny*nz; seeded random spheres (radius r_range, solid fraction
     solid_frac) kept out of x < x_free; walls at y = 0, ny-1, z = 0, nz-1;
     the x = 0 face is solid except a centred inlet x inlet patch of held
-    cells (liquid RHO_LIQ / 0.01 moving at u_in along +x); the x = nx-1 face
-    is held at the ambient gas state (an open outlet).  Gas: component 0 at
-    RHO_VAP, component 1 at 1.0.  Component 0 wets the solid (g_ads).
+    cells (component 0 at RHO_LIQ, component 1 at rho_gas_in, both moving at
+    u_in along +x); the x = nx-1 face is held at the ambient gas state (an
+    open outlet).  Gas: component 0 at RHO_VAP, component 1 at 1.0.
+    Component 0 wets the solid (g_ads).  The injected liquid carries some of
+    the second component (rho_gas_in = 0.1): with much less (0.01) the
+    nearly empty component's velocity F / rho at the inlet grows without
+    bound and the run diverges within a hundred steps.
     """
     nx, ny, nz = n
     ct = np.zeros((nz, ny, nx), dtype=np.uint8)
@@ -134,7 +138,7 @@ def porous_injection(n=(256, 256, 256), seed=1510035601, solid_frac=0.30, r_rang
     rho[1] = 1.0
     u = np.zeros((2, 3, nz, ny, nx), dtype=np.float32)
     rho[0, z0:z0 + inlet, y0:y0 + inlet, 0] = f32(RHO_LIQ)
-    rho[1, z0:z0 + inlet, y0:y0 + inlet, 0] = f32(0.01)
+    rho[1, z0:z0 + inlet, y0:y0 + inlet, 0] = f32(rho_gas_in)
     u[:, 0, z0:z0 + inlet, y0:y0 + inlet, 0] = f32(u_in)
     amb = (f32(RHO_VAP), 1.0)
     return _case(ct, rho, u, amb, ncomp=2, periodic=(0, 0, 0), progressive=progressive,
