@@ -127,9 +127,11 @@ def device_uuid(torch, dev):
         return None
 
 
-def make_case(S=None):
+def make_case(S=None, size=256):
     from paper_1510_03560_gb300 import workloads as W
     kw = {} if S is None else {"S": S}
+    if size != 256:
+        kw.update(n=(size, size, size), inlet=size // 4, x_free=max(size // 16, 4))
     return W.porous_injection(**kw)
 
 
@@ -157,6 +159,7 @@ def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid):
     out = dict(
         ms=ms,
         cells=st1["cell_updates"] - st0["cell_updates"],
+        fluid=st1["fluid_updates"] - st0["fluid_updates"],
         launches=st1["launches"] - st0["launches"],
         kernel_ms=[b - a for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
         kernel_launches=[b - a for a, b in zip(st0["kernel_launches"], st1["kernel_launches"])],
@@ -217,12 +220,14 @@ def dist_setup():
     return dist, dist.get_rank(), ws
 
 
-def reduce_max_sum(dist, torch, vmax, vsum):
+def reduce_max_sum(dist, torch, vmax, vsum, device="cuda"):
+    """Whole-job figures of N replicas: the slowest rank's time, the sum of
+    the work."""
     if dist is None:
         return vmax, vsum
-    t = torch.tensor([vmax], dtype=torch.float64, device="cuda")
+    t = torch.tensor([vmax], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    s = torch.tensor([vsum], dtype=torch.float64, device="cuda")
+    s = torch.tensor([vsum], dtype=torch.float64, device=device)
     dist.all_reduce(s, op=dist.ReduceOp.SUM)
     return float(t.item()), float(s.item())
 
@@ -263,6 +268,10 @@ def main():
     ap.add_argument("--no-static", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=256,
+                    help="grid edge (profiling captures use a smaller grid; the metric is 256)")
+    ap.add_argument("--static-only", action="store_true",
+                    help="time the static mesh only (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -280,8 +289,15 @@ def main():
         dist.barrier()
     from paper_1510_03560_gb300 import lbm as L
     uuid = device_uuid(torch, local)
-    case = make_case(args.S)
+    case = make_case(args.S, args.size)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    if args.static_only:
+        st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid)
+        if rank == 0:
+            print(json.dumps({"static_mlups": st["cells"] / (st["ms"] * 1e-3) / 1e6,
+                              "ms": st["ms"], "kernel_ms": st["kernel_ms"],
+                              "kernel_launches": st["kernel_launches"]}), flush=True)
+        return 0
 
     if dist is not None:
         dist.barrier()
@@ -307,13 +323,15 @@ def main():
 
     peak, peak_kind = peaks()
     mlups = cells_sum / (t_max * 1e-3) / 1e6
-    step_frac = prog["cells"] * BYTES_PER_UPDATE / (prog["ms"] * 1e-3) / 1e9 / peak
-    # dominant kernel: force + collide (kind 2); algorithmic bytes per launch =
-    # 304 B x meshed cells of that launch
+    # algorithmic bytes: 304 B for every fluid cell updated (solid cells move
+    # no data, held cells are read by their neighbours but never written)
+    step_frac = prog["fluid"] * BYTES_PER_UPDATE / (prog["ms"] * 1e-3) / 1e9 / peak
+    # dominant kernel: force + collide (kind 2)
     kms, kn = prog["kernel_ms"][2], prog["kernel_launches"][2]
-    coll_gbs = prog["cells"] * BYTES_PER_UPDATE / (kms * 1e-3) / 1e9 if kms > 0 else None
+    coll_gbs = prog["fluid"] * BYTES_PER_UPDATE / (kms * 1e-3) / 1e9 if kms > 0 else None
     traffic_pc = kernel_traffic()
     avg_cells = prog["cells"] / max(kn, 1)
+    avg_fluid = prog["fluid"] / max(kn, 1)
     roofline = {
         "bound": "hbm", "achieved": round(coll_gbs, 1) if coll_gbs else None,
         "peak": peak, "unit": "GB/s",
@@ -321,17 +339,19 @@ def main():
         "traffic": round(traffic_pc * avg_cells) if traffic_pc else None,
         "kernel": "k_collide (force gather + exact-difference collision + pull streaming)",
         "peak_kind": peak_kind,
-        "algorithmic_bytes_per_launch": round(avg_cells * BYTES_PER_UPDATE),
+        "algorithmic_bytes_per_launch": round(avg_fluid * BYTES_PER_UPDATE),
         "avg_launch_ms": round(kms / max(kn, 1), 5),
     }
     share = {name: round(v / max(sum(prog["kernel_ms"]), 1e-9), 4)
              for name, v in zip(("macro", "activate", "collide", "other"), prog["kernel_ms"])}
     config = {
-        "workload": WORKLOAD, "mode": "progressive", "grid": [256, 256, 256], "block": [8, 8, 8],
+        "workload": WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}",
+        "mode": "progressive", "grid": [args.size] * 3, "block": [8, 8, 8],
         "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
         "mean_active_fraction": round(prog["cells"] / 512 / args.steps / prog["total_blocks"], 4),
         "step_hbm_frac": round(step_frac, 4), "kernel_time_share": share,
+        "fluid_mlups": round(prog["fluid"] / (prog["ms"] * 1e-3) / 1e6, 1),
         "l2": "256 MiB buffer written before every timed step; flush outside the timed events",
         "parallelism": f"replicas x{world}",
     }
@@ -339,7 +359,7 @@ def main():
         s_mlups = s_cells / (s_max * 1e-3) / 1e6
         config["static_mlups"] = round(s_mlups, 1)
         config["static_step_hbm_frac"] = round(
-            stat["cells"] * BYTES_PER_UPDATE / (stat["ms"] * 1e-3) / 1e9 / peak, 4)
+            stat["fluid"] * BYTES_PER_UPDATE / (stat["ms"] * 1e-3) / 1e9 / peak, 4)
         config["progressive_over_static_time"] = round(prog["ms"] / stat["ms"], 4)
     cpu = None
     if not args.no_cpu:

@@ -99,6 +99,7 @@ typedef struct lbm_stats {
     long long total_blocks;     /* blocks of the grid */
     long long nonsolid_blocks;  /* blocks holding at least one non-solid cell */
     long long cell_updates;     /* sum over completed steps of 512 x active blocks */
+    long long fluid_updates;    /* sum over completed steps of the fluid cells of active blocks */
     long long launches;         /* kernels this context has launched */
     long long device_bytes;     /* device memory held by the context */
     double kernel_ms[4];        /* with profiling on: device time per kernel kind

@@ -702,6 +702,7 @@ int lbm_get_stats(lbm_ctx *c, lbm_stats *out)
         flush_profile(c);
         out->active_blocks = ctrl.n_active[c->step & 1];
         out->cell_updates = (long long)ctrl.cell_updates;
+        out->fluid_updates = (long long)ctrl.fluid_updates;
         long long ns = 0;
         for (int v : c->nonsolid_h) ns += v > 0;
         out->nonsolid_blocks = ns;

@@ -27,7 +27,8 @@ struct Ctrl {
     int ncand[2];      // candidate blocks found by the criterion
     int status;        // 0, or an LBM_E* code raised on the device
     int fail_step;     // step at which status was raised
-    unsigned long long cell_updates;
+    unsigned long long cell_updates;   // 512 x meshed blocks, summed over steps
+    unsigned long long fluid_updates;  // fluid cells of meshed blocks, summed over steps
     float psi_amb;     // psi of the ambient density, evaluated on the device
     int pad;
 };

@@ -502,6 +502,11 @@ __global__ void __launch_bounds__(CELLS) k_collide(KParams kp, int step)
     for (int slot = blockIdx.x; slot < n; slot += gridDim.x) {
         const int gid = kp.block_of[slot];
         load_neighbourhood(kp, gid, slot, INT_MAX, nb);
+        if (threadIdx.x == 0) {
+            int nf = 0;
+            for (int w = 0; w < MASK_WORDS; ++w) nf += __popc(~(nb.solid[13][w] | nb.held[w]));
+            atomicAdd(&ctrl->fluid_updates, (unsigned long long)nf);
+        }
         const bool solid = is_solid(nb, 13, c);
         const bool held = (nb.held[c >> 5] >> (c & 31)) & 1u;
         if (!solid && !held) {

@@ -47,7 +47,8 @@ class Stats(C.Structure):
     _fields_ = [
         ("steps", C.c_longlong), ("active_blocks", C.c_longlong), ("capacity", C.c_longlong),
         ("total_blocks", C.c_longlong), ("nonsolid_blocks", C.c_longlong),
-        ("cell_updates", C.c_longlong), ("launches", C.c_longlong), ("device_bytes", C.c_longlong),
+        ("cell_updates", C.c_longlong), ("fluid_updates", C.c_longlong),
+        ("launches", C.c_longlong), ("device_bytes", C.c_longlong),
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_longlong * 4),
     ]
 
