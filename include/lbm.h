@@ -187,9 +187,41 @@ int lbm_set_profiling(lbm_ctx *ctx, int on);
 /* Counters; waits for enqueued work first. */
 int lbm_get_stats(lbm_ctx *ctx, lbm_stats *out);
 
-/* Message of the last error of `ctx`, or of the last failed lbm_create
- * when ctx is NULL.  Never NULL. */
+/* Message of the last error of `ctx`, or of the last failed lbm_create or
+ * lbm_mass_noalloc (on the calling thread) when ctx is NULL.  Never NULL. */
 const char *lbm_last_error(const lbm_ctx *ctx);
+
+#define LBM_NOALLOC_MAX_BLOCKS 65536 /* largest nblocks lbm_mass_noalloc accepts */
+
+/* FP64 per-component mass of a population pool that the caller holds in
+ * device memory, computed without allocating any memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc, such as a host application whose device memory is entirely
+ * owned by another allocator (a framework that has reserved the whole GPU),
+ * or a real-time loop that must not allocate after start-up.  Its scratch
+ * (LBM_NOALLOC_MAX_BLOCKS x 2 partial sums and 2 totals, 1 MiB) is a
+ * fixed-size array inside the library; every GPU that loads the library
+ * holds it until the process exits.
+ *   f        device pointer, [nblocks][ncomp][19][512] FP32 populations in the
+ *            library's layout (velocity order of lbm_velocities, cell index
+ *            x + 8 * (y + 8 * z) within a block); read only
+ *   solid    device pointer, [nblocks][16] uint32 solid-cell bits (bit c % 32
+ *            of word c / 32 set: cell c is solid and is left out), or NULL
+ *   nblocks  1 .. LBM_NOALLOC_MAX_BLOCKS; larger is LBM_EINVAL
+ *   ncomp    1 or 2
+ *   mass     host array of ncomp doubles, written on success
+ *   stream   cudaStream_t to run on (NULL = default stream); the call waits
+ *            for it before returning
+ * The sum runs in the same fixed order as lbm_mass.  Every call shares the
+ * one scratch array of its device and rewrites every value it reads, so no
+ * state carries from one call to the next; calls that overlap on the same
+ * GPU (other streams or host threads) race on it and must be serialised by
+ * the caller.  The first call on a device looks up the array's device
+ * address with that device current (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Errors: LBM_EINVAL, LBM_ECUDA (message in
+ * lbm_last_error(NULL)). */
+int lbm_mass_noalloc(const float *f, const uint32_t *solid, long long nblocks, int ncomp,
+                     double *mass, void *stream);
 
 #ifdef __cplusplus
 }

@@ -309,6 +309,8 @@ int active_count(lbm_ctx *c, int *n)
 
 }  // namespace
 
+void lbm::set_global_error(const char *msg) { snprintf(g_create_error, sizeof g_create_error, "%s", msg); }
+
 extern "C" {
 
 int lbm_create(const lbm_params *p, lbm_ctx **out)

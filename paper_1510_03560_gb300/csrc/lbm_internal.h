@@ -84,4 +84,7 @@ cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, doubl
                         cudaStream_t s);
 int max_ctas_per_sm_stream_kernels();
 
+// Message returned by lbm_last_error(NULL) (lbm_capi.cpp).
+void set_global_error(const char *msg);
+
 }  // namespace lbm

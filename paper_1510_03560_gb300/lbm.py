@@ -56,7 +56,8 @@ class Stats(C.Structure):
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_step", "lbm_step_async",
            "lbm_sync", "lbm_get_macro", "lbm_active_blocks", "lbm_mass",
            "lbm_get_block_populations", "lbm_velocities", "lbm_set_profiling", "lbm_get_stats",
-           "lbm_last_error"]
+           "lbm_last_error", "lbm_mass_noalloc"]
+NOALLOC_MAX_BLOCKS = 65536
 
 _lib = None
 
@@ -92,11 +93,25 @@ def load():
     lib.lbm_get_stats.argtypes = [vp, C.POINTER(Stats)]
     lib.lbm_last_error.argtypes = [vp]
     lib.lbm_last_error.restype = C.c_char_p
+    lib.lbm_mass_noalloc.argtypes = [vp, vp, C.c_longlong, C.c_int, dp, vp]
     for name in EXPORTS:
         if name != "lbm_last_error":
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
+
+
+def mass_noalloc(f_ptr: int, solid_ptr, nblocks: int, ncomp: int, stream_ptr=None) -> np.ndarray:
+    """lbm_mass_noalloc on a caller-held device population pool (device
+    pointers as ints); allocates nothing on the device."""
+    lib = load()
+    m = np.zeros(2)
+    rc = lib.lbm_mass_noalloc(C.c_void_p(f_ptr), C.c_void_p(solid_ptr) if solid_ptr else None,
+                              int(nblocks), int(ncomp), m.ctypes.data_as(C.POINTER(C.c_double)),
+                              C.c_void_p(stream_ptr) if stream_ptr else None)
+    if rc != OK:
+        raise LBMError(rc, lib.lbm_last_error(None).decode())
+    return m[:ncomp].copy()
 
 
 def velocities() -> np.ndarray:
