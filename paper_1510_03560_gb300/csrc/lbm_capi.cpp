@@ -264,16 +264,15 @@ int read_ctrl(lbm_ctx *c, Ctrl &out)
 
 int enqueue_steps(lbm_ctx *c, int nsteps)
 {
-    const int grid = persistent_grid(c);
     for (int k = 0; k < nsteps; ++k) {
         const int t = (int)(c->step + k);
         CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
-                         return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, grid, c->stream);
+                         return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
                      }));
         if (c->p.progressive)
             CUDA_OR_FAIL(c, timed(c, K_ACTIVATE,
                                   [&] { return launch_activate(c->kp, t, c->sms, c->stream); }));
-        CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, grid, c->stream); }));
+        CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, c->sms, c->stream); }));
     }
     c->step += nsteps;
     return LBM_OK;
@@ -352,7 +351,9 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
         size_t bytes;
     } want[] = {
         {(void **)&k.f, 2 * k.buf_stride * sizeof(float)},
-        {(void **)&k.mac, (size_t)c->capacity * MACS * CELLS * sizeof(float)},
+        {(void **)&k.mac, (size_t)c->capacity * CELLS * sizeof(float4)},
+        {(void **)&k.nbits, (size_t)c->capacity * CELLS * sizeof(uint32_t)},
+        {(void **)&k.nbr, (size_t)c->capacity * NBR_STRIDE * sizeof(int)},
         {(void **)&k.uprev, p->progressive ? (size_t)c->capacity * p->ncomp * 3 * CELLS * sizeof(float) : 0},
         {(void **)&k.slot_of, (size_t)c->nblocks * sizeof(int)},
         {(void **)&k.block_of, (size_t)c->capacity * sizeof(int)},
@@ -474,8 +475,32 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
         k.rho_amb[a] = a < nc ? rho_amb[a] : 0.f;
         for (int i = 0; i < Q; ++i) k.famb[a][i] = weight_f(i) * k.rho_amb[a];
     }
+    // neighbour-slot rows of the initial slots (k = dx+1 + 3(dy+1) + 9(dz+1))
+    std::vector<int> nbr_rows((size_t)std::max(n0, 1) * NBR_STRIDE, SOLIDBLK);
+    for (int sl = 0; sl < n0; ++sl) {
+        const int b = block_of[sl];
+        const int bx = b % c->nbx, by = (b / c->nbx) % c->nby, bz = b / (c->nbx * c->nby);
+        for (int kk = 0; kk < 27; ++kk) {
+            int q[3] = {bx + kk % 3 - 1, by + (kk / 3) % 3 - 1, bz + kk / 9 - 1};
+            const int nq[3] = {c->nbx, c->nby, c->nbz};
+            bool outside = false;
+            for (int a = 0; a < 3; ++a) {
+                if (q[a] < 0 || q[a] >= nq[a]) {
+                    if (!p.periodic[a]) outside = true;
+                    q[a] = (q[a] + nq[a]) % nq[a];
+                }
+            }
+            int v = SOLIDBLK;
+            if (kk == 13) v = sl;
+            else if (!outside) v = slot_of[q[0] + c->nbx * ((long long)q[1] + (long long)c->nby * q[2])];
+            nbr_rows[(size_t)sl * NBR_STRIDE + kk] = v;
+        }
+    }
     cudaStream_t s = c->stream;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(k.slot_of, slot_of.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (n0)
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(k.nbr, nbr_rows.data(), (size_t)n0 * NBR_STRIDE * sizeof(int),
+                                        cudaMemcpyHostToDevice, s));
     if (n0)
         CUDA_OR_FAIL(c, cudaMemcpyAsync(k.block_of, block_of.data(), n0 * sizeof(int), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.solid, c->solid_h.data(), nb * MASK_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
@@ -579,14 +604,13 @@ int lbm_get_macro(lbm_ctx *c, int comp, float *rho, float *ux, float *uy, float 
     std::vector<int> block_of(n);
     CUDA_OR_FAIL(c, cudaMemcpyAsync(block_of.data(), c->kp.block_of, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     const int rd = (int)(c->step & 1);
-    const int grid = persistent_grid(c);
-    CUDA_OR_FAIL(c, launch_macro(c->kp, (int)c->step, 0, grid, c->stream));
+    CUDA_OR_FAIL(c, launch_macro(c->kp, (int)c->step, 0, c->sms, c->stream));
     c->launches += 1;
     const int per_chunk = (int)(c->stage_floats / (4 * CELLS));
     std::vector<float> host((size_t)per_chunk * 4 * CELLS);
     for (int s0 = 0; s0 < n; s0 += per_chunk) {
         const int m = std::min(per_chunk, n - s0);
-        CUDA_OR_FAIL(c, launch_output(c->kp, rd, comp, s0, m, c->stage, std::min(m, grid), c->stream));
+        CUDA_OR_FAIL(c, launch_output(c->kp, rd, comp, s0, m, c->stage, c->sms, c->stream));
         c->launches += 1;
         CUDA_OR_FAIL(c, cudaMemcpyAsync(host.data(), c->stage, (size_t)m * 4 * CELLS * sizeof(float),
                                         cudaMemcpyDeviceToHost, c->stream));

@@ -12,8 +12,9 @@ namespace lbm {
 constexpr int EDGE = 8;     // cells per block edge
 constexpr int CELLS = 512;  // cells per block
 constexpr int Q = 19;       // D3Q19
-constexpr int MACS = 3;     // per-cell scratch written by the stream pass: rho0, psi0, rho1
 constexpr int MASK_WORDS = CELLS / 32;
+constexpr int HELD_BIT = 19;  // bit of a cell's neighbour word marking a held cell
+constexpr int NBR_STRIDE = 32; // ints per row of the neighbour-slot table (27 used)
 
 // slot_of[] values besides a slot index
 constexpr int AMBIENT = -1;  // unmeshed block (at least one non-solid cell)
@@ -29,6 +30,7 @@ struct Ctrl {
     int fail_step;     // step at which status was raised
     unsigned long long cell_updates;   // 512 x meshed blocks, summed over steps
     unsigned long long fluid_updates;  // fluid cells of meshed blocks, summed over steps
+    unsigned long long fluid_active;   // fluid cells of the meshed blocks now
     float psi_amb;     // psi of the ambient density, evaluated on the device
     int pad;
 };
@@ -54,9 +56,12 @@ struct KParams {
     float famb[2][Q];   // ambient resting populations w_i rho_amb
     // device memory
     float *f;           // [2][capacity][ncomp][Q][CELLS]
-    float *mac;         // [capacity][MACS][CELLS]
+    float4 *mac;        // [capacity][CELLS]: rho0, psi0, rho1, 0 of the current step
+    uint32_t *nbits;    // [capacity][CELLS]: bit i set when cell x - e_i is solid
+                        // (bit 0: the cell itself), bit HELD_BIT: held cell
     float *uprev;       // [capacity][ncomp][3][CELLS]
     int *slot_of;       // [nblocks]
+    int *nbr;           // [capacity][NBR_STRIDE]: slots of the 27 blocks around a slot
     int *block_of;      // [capacity]
     const uint32_t *solid;  // [nblocks][MASK_WORDS]
     const uint32_t *held;   // [nblocks][MASK_WORDS]
@@ -75,11 +80,13 @@ enum KernelKind { K_MACRO = 0, K_ACTIVATE = 1, K_COLLIDE = 2, K_OTHER = 3 };
 cudaError_t launch_init(const KParams &kp, const float *in_block, int slot0, int nslots,
                         int grid, cudaStream_t s);
 cudaError_t launch_ambient_psi(const KParams &kp, cudaStream_t s);
-cudaError_t launch_macro(const KParams &kp, int step, int criterion, int grid, cudaStream_t s);
-cudaError_t launch_activate(const KParams &kp, int step, int grid, cudaStream_t s);
-cudaError_t launch_collide(const KParams &kp, int step, int grid, cudaStream_t s);
+// The cell kernels size their persistent grids themselves: `sms` x the
+// CTAs per SM their occupancy allows.
+cudaError_t launch_macro(const KParams &kp, int step, int criterion, int sms, cudaStream_t s);
+cudaError_t launch_activate(const KParams &kp, int step, int sms, cudaStream_t s);
+cudaError_t launch_collide(const KParams &kp, int step, int sms, cudaStream_t s);
 cudaError_t launch_output(const KParams &kp, int rd, int comp, int slot0, int nslots, float *out,
-                          int grid, cudaStream_t s);
+                          int sms, cudaStream_t s);
 cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, double *out, int grid,
                         cudaStream_t s);
 int max_ctas_per_sm_stream_kernels();

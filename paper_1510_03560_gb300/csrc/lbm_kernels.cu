@@ -5,15 +5,21 @@
 // coalescing):
 //   f[buf][slot][comp][dir][cell]   FP32 populations, two buffers (A-B
 //                                   pattern, Sec. 3), cell = x + 8 (y + 8 z)
-//   mac[slot][3][cell]              rho0, psi0, rho1 of the current step
+//   mac[slot][cell]                 float4 (rho0, psi0, rho1, 0) of the step
+//   nbits[slot][cell]               bit i: cell x - e_i is solid; bit 19: held
 //   uprev[slot][comp][3][cell]      velocity of the previous step, read and
 //                                   written only at cells bordering
 //                                   unmeshed blocks (criterion, Eq. 13)
-// A warp covers four x-rows of one z-plane of a block, so each population
+// A warp covers four x-rows of one z-plane of a block: every population
 // access of a warp touches 4 consecutive 32-byte sectors of one plane.
 //
-// One time step is three launches, each a grid-stride loop of one CTA
-// (512 threads, one per cell) per meshed block:
+// The step kernels have no block-wide barrier.  A CTA of 256 threads works on
+// half a block at a time (grid-stride over half-blocks); every warp fetches
+// the slots of the 27 blocks around its block with one lane-parallel load
+// and hands them out with shuffles, and reads the per-cell solid bits
+// instead of block masks.
+//
+// One time step is three launches:
 //   k_macro    pull streaming + Eqs. 4-5 + Eqs. 6-7 -> mac; criterion of
 //              Eq. 13 at cells bordering unmeshed blocks, marking targets
 //   k_activate new blocks: slots, ambient equilibrium, their k_macro work
@@ -28,6 +34,10 @@
 
 namespace lbm {
 namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int THREADS = 256;            // threads per CTA of the cell kernels
+constexpr int PARTS = CELLS / THREADS;  // CTA work items per block
 
 // ---- D3Q19 in this library's order: the 9 velocities with e_z = 0, then
 // the 5 with e_z = +1, then the 5 with e_z = -1; opposites are adjacent
@@ -54,12 +64,32 @@ __host__ __device__ constexpr float wgt(int i)
     return i == 0 ? 1.0f / 3.0f
                   : ((i <= 4 || i == 9 || i == 14) ? 1.0f / 18.0f : 1.0f / 36.0f);
 }
-// One representative of each opposite pair.
+// One representative of each opposite pair, and the representative of any
+// moving velocity's pair.
 __host__ __device__ constexpr int pair_rep(int p)
 {
     return p < 4 ? 1 + 2 * p : 5 + p;  // 1 3 5 7 | 9 10 11 12 13
 }
+__host__ __device__ constexpr int rep_of(int i)
+{
+    return i <= 8 ? ((i & 1) ? i : i - 1) : (i <= 13 ? i : i - 5);
+}
 constexpr int NPAIR = 9;
+
+template <int I, int N>
+struct Unroll {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&f)
+    {
+        f.template operator()<I>();
+        Unroll<I + 1, N>::run(f);
+    }
+};
+template <int N>
+struct Unroll<N, N> {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&) {}
+};
 
 // Neighbour-block index (0..26) of a local coordinate in [-1, 8].
 __device__ __forceinline__ int side(int v) { return v < 0 ? 0 : (v > 7 ? 2 : 1); }
@@ -68,15 +98,6 @@ __device__ __forceinline__ int lcell(int x, int y, int z)
 {
     return (x & 7) | ((y & 7) << 3) | ((z & 7) << 6);
 }
-
-// The 3 x 3 x 3 neighbourhood of the block a CTA is working on.
-struct Nbr {
-    int slot[27];                     // slot, AMBIENT or SOLIDBLK
-    uint32_t solid[27][MASK_WORDS];   // solid cells (all set outside the domain)
-    uint32_t held[MASK_WORDS];        // held cells of the centre block
-    unsigned amb_bits;                // bit k: neighbour k is unmeshed
-    unsigned tgt_bits;                // bit k: the criterion fired towards k
-};
 
 __device__ __forceinline__ int neighbour_block(const KParams &kp, int x, int y, int z)
 {
@@ -97,53 +118,48 @@ __device__ __forceinline__ int neighbour_block(const KParams &kp, int x, int y, 
 
 __device__ __forceinline__ int neighbour_of(const KParams &kp, int gid, int k)
 {
-    int bx = gid % kp.nbx, by = (gid / kp.nbx) % kp.nby, bz = gid / (kp.nbx * kp.nby);
+    const int bx = gid % kp.nbx, by = (gid / kp.nbx) % kp.nby, bz = gid / (kp.nbx * kp.nby);
     return neighbour_block(kp, bx + k % 3 - 1, by + (k / 3) % 3 - 1, bz + k / 9 - 1);
 }
 
-// Fill `nb` for block `gid` held in `own_slot`.  Neighbours whose slot is
-// >= slot_limit count as unmeshed (blocks created in the current step,
-// seen from the block-creation kernel).  Ends with a barrier.
-__device__ void load_neighbourhood(const KParams &kp, int gid, int own_slot, int slot_limit,
-                                   Nbr &nb)
+// The 27 blocks around `gid`, one slot per lane (lane 13: the block itself,
+// or unmeshed with own_unmeshed; lanes 27-31: SOLIDBLK), and the
+// warp-uniform mask of unmeshed neighbours.  Slots >= slot_limit count as
+// unmeshed.  Every lane of the warp calls it.
+struct WarpNbr {
+    int slot;
+    unsigned amb;
+};
+
+__device__ __forceinline__ WarpNbr warp_nbr(const KParams &kp, int gid, int own_slot, int slot_limit,
+                                            bool own_unmeshed = false)
 {
-    const int t = threadIdx.x;
-    if (t < 27) {
-        int s;
-        if (t == 13) {
-            s = own_slot;
-        } else {
-            int nid = neighbour_of(kp, gid, t);
-            if (nid < 0) {
-                s = SOLIDBLK;
-            } else {
-                s = kp.slot_of[nid];
-                if (s >= slot_limit) s = AMBIENT;
-            }
+    const int lane = threadIdx.x & 31;
+    int s = SOLIDBLK;
+    if (lane == 13) {
+        s = own_unmeshed ? AMBIENT : own_slot;
+    } else if (lane < 27) {
+        const int nid = neighbour_of(kp, gid, lane);
+        if (nid >= 0) {
+            s = kp.slot_of[nid];
+            if (s >= slot_limit) s = AMBIENT;
         }
-        nb.slot[t] = s;
     }
-    for (int w = t; w < 27 * MASK_WORDS; w += blockDim.x) {
-        int k = w / MASK_WORDS, word = w % MASK_WORDS;
-        int nid = k == 13 ? gid : neighbour_of(kp, gid, k);
-        nb.solid[k][word] = nid < 0 ? 0xffffffffu : kp.solid[(size_t)nid * MASK_WORDS + word];
-    }
-    if (t < MASK_WORDS) nb.held[t] = kp.held[(size_t)gid * MASK_WORDS + t];
-    __syncthreads();
-    if (t == 0) {
-        unsigned bits = 0;
-        for (int k = 0; k < 27; ++k)
-            if (nb.slot[k] == AMBIENT) bits |= 1u << k;
-        nb.amb_bits = bits;
-        nb.tgt_bits = 0;
-    }
-    __syncthreads();
+    return WarpNbr{s, __ballot_sync(FULL, s == AMBIENT) & ~(1u << 13)};
 }
 
-__device__ __forceinline__ bool is_solid(const Nbr &nb, int k, int lc)
+// The same, read from the slot's row of the neighbour-slot table (kept up to
+// date by block creation): one coalesced 128-byte load per warp.
+__device__ __forceinline__ int nbr_row_lane(const KParams &kp, int slot)
 {
-    return (nb.solid[k][lc >> 5] >> (lc & 31)) & 1u;
+    return kp.nbr[(size_t)slot * NBR_STRIDE + (threadIdx.x & 31)];
 }
+__device__ __forceinline__ WarpNbr warp_nbr_of(int lane_slot)
+{
+    return WarpNbr{lane_slot, __ballot_sync(FULL, lane_slot == AMBIENT) & ~(1u << 13)};
+}
+
+__device__ __forceinline__ int nb_slot(const WarpNbr &w, int k) { return __shfl_sync(FULL, w.slot, k); }
 
 // Neighbour blocks reachable from a cell through the 18 moving velocities.
 __device__ __forceinline__ unsigned reach_bits(int lx, int ly, int lz)
@@ -154,58 +170,98 @@ __device__ __forceinline__ unsigned reach_bits(int lx, int ly, int lz)
     return r & ~(1u << 13);
 }
 
-// Pull streaming of one component into fin (Eq. 10 left-hand side): the
-// population moving along e_i arrives from x - e_i; halfway bounce-back
-// when that cell is solid (or outside), the ambient resting population
-// when it lies in an unmeshed block.  Held cells keep their own
-// populations.
-__device__ __forceinline__ void pull(const KParams &kp, const Nbr &nb, const float *rdbuf,
-                                     int own_slot, int a, int c, int lx, int ly, int lz,
-                                     bool held, float fin[Q])
+// Solid / held word of one cell from the per-block masks (bit i: x - e_i is
+// solid, cells outside a non-periodic axis are solid; bit HELD_BIT: held).
+__device__ uint32_t cell_bits(const KParams &kp, int gid, int c)
 {
-    const float *own = rdbuf + (size_t)own_slot * kp.slot_floats + a * Q * CELLS;
-    if (held) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i) fin[i] = own[i * CELLS + c];
-        return;
-    }
+    const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+    uint32_t bits = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const int sx = lx - cx(i), sy = ly - cy(i), sz = lz - cz(i);
-        const int k = nbk(sx, sy, sz);
-        const int lc = lcell(sx, sy, sz);
-        float v;
-        if (is_solid(nb, k, lc)) {
-            v = own[opp(i) * CELLS + c];
-        } else {
-            const int s = nb.slot[k];
-            v = s >= 0 ? rdbuf[(size_t)s * kp.slot_floats + a * Q * CELLS + i * CELLS + lc]
-                       : kp.famb[a][i];
-        }
-        fin[i] = v;
+        const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+        const int nid = k == 13 ? gid : neighbour_of(kp, gid, k);
+        const bool solid =
+            nid < 0 || ((kp.solid[(size_t)nid * MASK_WORDS + (lc >> 5)] >> (lc & 31)) & 1u);
+        bits |= (uint32_t)solid << i;
     }
+    if ((kp.held[(size_t)gid * MASK_WORDS + (c >> 5)] >> (c & 31)) & 1u) bits |= 1u << HELD_BIT;
+    return bits;
 }
 
-// Eqs. 4-5: density and momentum (opposite pairs differenced first).
-__device__ __forceinline__ void moments(const float fin[Q], float &rho, float j[3])
+// Pull streaming (Eq. 10, left-hand side) of every component of one cell,
+// rest first, then opposite pairs, handing each arriving population to
+// sink(a, I, v).  The population moving along e_I comes from x - e_I:
+// halfway bounce-back when that cell is solid, the ambient resting
+// population when its block is unmeshed, the stored value otherwise; held
+// cells keep their own.  With own_ambient the cell's own block is one created
+// in this step, still at the ambient state, and is not read back.  All lanes
+// must call (shuffles); `live` masks the loads.
+template <int NC, class Sink>
+__device__ __forceinline__ void pull(const KParams &kp, const WarpNbr &wn, const float *rd,
+                                     int own_slot, int c, int lx, int ly, int lz, uint32_t bits,
+                                     bool live, bool own_ambient, Sink &&sink)
 {
-    float r = 0.f;
+    const float *own = rd + (size_t)own_slot * kp.slot_floats + c;
+    const bool held = (bits >> HELD_BIT) & 1u;
+    // Every population is one unconditional (predicated) load from an address
+    // chosen without branching, so that all of a cell's loads can be in
+    // flight together; the ambient value replaces the loaded one afterwards.
+    auto one = [&]<int I>() {
+        const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+        const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+        const int s = nb_slot(wn, k);
+        const bool bounce = (bits >> I) & 1u;
+        bool from_nb, amb;
+        const float *p;
+        if (own_ambient) {
+            from_nb = s >= 0 && !bounce;
+            amb = !from_nb;
+            p = from_nb ? rd + (size_t)s * kp.slot_floats + I * CELLS + lc : own + I * CELLS;
+        } else {
+            from_nb = !held && !bounce && s >= 0;
+            amb = !held && !bounce && s < 0;
+            p = from_nb ? rd + (size_t)s * kp.slot_floats + I * CELLS + lc
+                        : own + ((held || amb) ? I : opp(I)) * CELLS;
+        }
+        const bool load = live && !amb;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) r += fin[i];
-    float jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int p = 0; p < NPAIR; ++p) {
-        const int i = pair_rep(p);
-        const float d = fin[i] - fin[opp(i)];
-        if (cx(i) > 0) jx += d; else if (cx(i) < 0) jx -= d;
-        if (cy(i) > 0) jy += d; else if (cy(i) < 0) jy -= d;
-        if (cz(i) > 0) jz += d; else if (cz(i) < 0) jz -= d;
-    }
-    rho = r;
-    j[0] = jx;
-    j[1] = jy;
-    j[2] = jz;
+        for (int a = 0; a < NC; ++a) {
+            float v = load ? __ldg(p + a * Q * CELLS) : 0.f;
+            if (live && amb) v = kp.famb[a][I];
+            sink.template operator()<I>(a, v);
+        }
+    };
+    one.template operator()<0>();
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        one.template operator()<pair_rep(P)>();
+        one.template operator()<opp(pair_rep(P))>();
+    });
 }
+
+// Eqs. 4-5 accumulated in pull order: the density as a running sum, the
+// momentum from each opposite pair's difference.
+struct Moments {
+    float rho[2] = {0.f, 0.f};
+    float j[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float first[2] = {0.f, 0.f};
+    template <int I>
+    __device__ __forceinline__ void add(int a, float v)
+    {
+        rho[a] += v;
+        if constexpr (I == 0) {
+            return;
+        } else if constexpr (rep_of(I) == I) {
+            first[a] = v;
+        } else {
+            constexpr int R = rep_of(I);
+            const float d = first[a] - v;
+            if (cx(R) > 0) j[a][0] += d; else if (cx(R) < 0) j[a][0] -= d;
+            if (cy(R) > 0) j[a][1] += d; else if (cy(R) < 0) j[a][1] -= d;
+            if (cz(R) > 0) j[a][2] += d; else if (cz(R) < 0) j[a][2] -= d;
+        }
+    }
+};
 
 // Eq. 7 (Peng-Robinson) and Eq. 6 (pseudo-potential), FP32.
 __device__ __forceinline__ float psi_of(const KParams &kp, float rho)
@@ -229,32 +285,22 @@ __device__ __forceinline__ float feq(float wrho, float ux, float uy, float uz, f
     return wrho * (1.f + 3.f * eu + 4.5f * eu * eu - 1.5f * uu);
 }
 
-template <int I, int N>
-struct Unroll {
-    template <class F>
-    __device__ __forceinline__ static void run(F &&f)
-    {
-        f.template operator()<I>();
-        Unroll<I + 1, N>::run(f);
-    }
-};
-template <int N>
-struct Unroll<N, N> {
-    template <class F>
-    __device__ __forceinline__ static void run(F &&) {}
-};
-
 // ---------------------------------------------------------------------------
 // Initial state: equilibrium of the initial fields in both buffers, the
-// initial velocity as the "previous" one.  in: [slot - slot0][ncomp][4][CELLS]
-// (rho, ux, uy, uz), block-major.
+// initial velocity as the "previous" one, the cells' solid words.
+// in: [slot - slot0][ncomp][4][CELLS] (rho, ux, uy, uz), block-major.
 __global__ void __launch_bounds__(CELLS) k_init(KParams kp, const float *in, int slot0, int nslots)
 {
     const int c = threadIdx.x;
     for (int r = blockIdx.x; r < nslots; r += gridDim.x) {
         const int slot = slot0 + r;
         const int gid = kp.block_of[slot];
-        const bool solid = (kp.solid[(size_t)gid * MASK_WORDS + (c >> 5)] >> (c & 31)) & 1u;
+        const uint32_t bits = cell_bits(kp, gid, c);
+        kp.nbits[(size_t)slot * CELLS + c] = bits;
+        const bool solid = bits & 1u;
+        const unsigned fluid = __ballot_sync(FULL, !solid && !((bits >> HELD_BIT) & 1u));
+        if ((c & 31) == 0 && fluid)
+            atomicAdd(&kp.ctrl->fluid_active, (unsigned long long)__popc(fluid));
         for (int a = 0; a < kp.ncomp; ++a) {
             const float *src = in + ((size_t)r * kp.ncomp + a) * 4 * CELLS;
             float rho = src[c], ux = src[CELLS + c], uy = src[2 * CELLS + c],
@@ -283,53 +329,66 @@ __global__ void k_ambient_psi(KParams kp)
     if (threadIdx.x == 0 && blockIdx.x == 0) kp.ctrl->psi_amb = psi_of(kp, kp.rho_amb[0]);
 }
 
-// Streaming + macroscopics of one cell of a meshed block into mac; returns
-// the bare velocities for the criterion.
+// Streaming + moments of one cell; writes mac (live cells), returns rho and
+// the bare velocity.  All lanes must call.
 template <int NC>
-__device__ __forceinline__ void macro_cell(const KParams &kp, const Nbr &nb, const float *rd,
-                                           int slot, int c, int lx, int ly, int lz, bool held,
-                                           float u[2][3])
+__device__ __forceinline__ void macro_cell(const KParams &kp, const WarpNbr &wn, const float *rd,
+                                           int slot, int c, int lx, int ly, int lz, uint32_t bits,
+                                           bool live, bool own_ambient, float rho[2], float u[2][3])
 {
-    float rho[2] = {0.f, 0.f};
+    Moments m;
+    pull<NC>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, own_ambient,
+             [&]<int I>(int a, float v) { m.template add<I>(a, v); });
 #pragma unroll
     for (int a = 0; a < NC; ++a) {
-        float fin[Q], j[3];
-        pull(kp, nb, rd, slot, a, c, lx, ly, lz, held, fin);
-        moments(fin, rho[a], j);
-        const float inv = 1.f / rho[a];
-        u[a][0] = j[0] * inv;
-        u[a][1] = j[1] * inv;
-        u[a][2] = j[2] * inv;
+        rho[a] = m.rho[a];
+        const float inv = 1.f / m.rho[a];
+        u[a][0] = m.j[a][0] * inv;
+        u[a][1] = m.j[a][1] * inv;
+        u[a][2] = m.j[a][2] * inv;
     }
-    float *m = kp.mac + (size_t)slot * MACS * CELLS + c;
-    m[0] = rho[0];
-    m[CELLS] = psi_of(kp, rho[0]);
-    if (NC == 2) m[2 * CELLS] = rho[1];
+    if (live)
+        kp.mac[(size_t)slot * CELLS + c] =
+            make_float4(rho[0], psi_of(kp, rho[0]), NC == 2 ? rho[1] : 0.f, 0.f);
 }
 
 // Pass 1 of a step: streaming and moments over the meshed blocks; with
 // `criterion`, Eq. 13 at fluid cells bordering unmeshed blocks.
 template <int NC>
-__global__ void __launch_bounds__(CELLS) k_macro(KParams kp, int step, int criterion)
+__global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int criterion)
 {
-    __shared__ Nbr nb;
     Ctrl *ctrl = kp.ctrl;
     if (criterion && ctrl->status) return;
     const int par = step & 1;
     const int n = ctrl->n_active[par];
     const float *rd = kp.f + (size_t)par * kp.buf_stride;
-    const int c = threadIdx.x, lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
-    const unsigned reach = reach_bits(lx, ly, lz);
-    for (int slot = blockIdx.x; slot < n; slot += gridDim.x) {
-        const int gid = kp.block_of[slot];
-        load_neighbourhood(kp, gid, slot, INT_MAX, nb);
-        const bool solid = is_solid(nb, 13, c);
-        const bool held = (nb.held[c >> 5] >> (c & 31)) & 1u;
-        if (!solid) {
-            float u[2][3];
-            macro_cell<NC>(kp, nb, rd, slot, c, lx, ly, lz, held, u);
-            const unsigned front = reach & nb.amb_bits;
-            if (criterion && !held && front) {
+    const int lane = threadIdx.x & 31;
+    const int total = n * PARTS;
+    // the neighbour row and solid word of the next item are fetched while
+    // the current one is processed
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+        }
+        const bool live = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        float rho[2], u[2][3];
+        macro_cell<NC>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, rho, u);
+        if (criterion) {
+            const unsigned front = reach_bits(lx, ly, lz) & wn.amb;
+            unsigned tgt = 0;
+            if (live && !held && front) {
                 float d2max = 0.f;
 #pragma unroll
                 for (int a = 0; a < NC; ++a) {
@@ -338,18 +397,20 @@ __global__ void __launch_bounds__(CELLS) k_macro(KParams kp, int step, int crite
                                 dz = u[a][2] - up[2 * CELLS];
                     d2max = fmaxf(d2max, dx * dx + dy * dy + dz * dz);
                 }
-                if (d2max > kp.S2) atomicOr(&nb.tgt_bits, front);
+                if (d2max > kp.S2) tgt = front;
+            }
+            tgt = __reduce_or_sync(FULL, tgt);
+            if (tgt && lane < 27 && ((tgt >> lane) & 1u)) {
+                // a candidate takes the next slot after the meshed ones now
+                // (k_activate checks the capacity and undoes it if full)
+                const int nid = neighbour_of(kp, kp.block_of[slot], lane);
+                if (atomicCAS(&kp.cand_mark[nid], 0u, 1u) == 0u) {
+                    const int pos = atomicAdd(&ctrl->ncand[par], 1);
+                    kp.cand_list[pos] = nid;
+                    if (n + pos < kp.capacity) kp.slot_of[nid] = n + pos;
+                }
             }
         }
-        __syncthreads();
-        if (criterion && threadIdx.x < 27 && ((nb.tgt_bits >> threadIdx.x) & 1u)) {
-            const int nid = neighbour_of(kp, gid, threadIdx.x);
-            if (atomicCAS(&kp.cand_mark[nid], 0u, 1u) == 0u) {
-                const int pos = atomicAdd(&ctrl->ncand[par], 1);
-                kp.cand_list[pos] = nid;
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -358,15 +419,21 @@ __global__ void __launch_bounds__(CELLS) k_macro(KParams kp, int step, int crite
 // buffers (R14) and get their streaming and moments of this step computed,
 // with every block created in this step seen as ambient.
 template <int NC>
-__global__ void __launch_bounds__(CELLS) k_activate(KParams kp, int step)
+__global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
 {
-    __shared__ Nbr nb;
     Ctrl *ctrl = kp.ctrl;
     if (ctrl->status) return;
     const int par = step & 1;
     const int n_old = ctrl->n_active[par];
     const int ncand = ctrl->ncand[par];
     if (n_old + ncand > kp.capacity) {
+        // the pool cannot hold them: undo the slots k_macro handed out, so
+        // the state stays that of the last completed step
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncand; k += gridDim.x * blockDim.x) {
+            const int gid = kp.cand_list[k];
+            kp.slot_of[gid] = AMBIENT;
+            kp.cand_mark[gid] = 0u;
+        }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             ctrl->status = LBM_ENOMEM;
             ctrl->fail_step = step;
@@ -378,13 +445,26 @@ __global__ void __launch_bounds__(CELLS) k_activate(KParams kp, int step)
         ctrl->ncand[par ^ 1] = 0;
     }
     const float *rd = kp.f + (size_t)par * kp.buf_stride;
-    const int c = threadIdx.x, lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
-    for (int k = blockIdx.x; k < ncand; k += gridDim.x) {
+    for (int it = blockIdx.x; it < ncand * PARTS; it += gridDim.x) {
+        const int k = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
         const int slot = n_old + k;
         const int gid = kp.cand_list[k];
-        if (threadIdx.x == 0) {
-            kp.block_of[slot] = gid;
-            kp.slot_of[gid] = slot;
+        if (c == 0) kp.block_of[slot] = gid;
+        if (c < 32) {
+            // the new block's row of the neighbour-slot table, and its slot in
+            // the rows of its meshed neighbours (every candidate's slot is
+            // already set, so the two writers of an entry agree)
+            int s = SOLIDBLK;
+            if (c == 13) {
+                s = slot;
+            } else if (c < 27) {
+                const int nid = neighbour_of(kp, gid, c);
+                if (nid >= 0) s = kp.slot_of[nid];
+                if (s >= 0) kp.nbr[(size_t)s * NBR_STRIDE + (26 - c)] = slot;
+            }
+            kp.nbr[(size_t)slot * NBR_STRIDE + c] = s;
         }
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
@@ -396,27 +476,27 @@ __global__ void __launch_bounds__(CELLS) k_activate(KParams kp, int step)
                 d1[i * CELLS] = kp.famb[a][i];
             }
         }
-        __syncthreads();  // the block's own populations are visible to the CTA
-        load_neighbourhood(kp, gid, slot, n_old, nb);
-        const bool solid = is_solid(nb, 13, c);
-        const bool held = (nb.held[c >> 5] >> (c & 31)) & 1u;
-        if (!solid) {
-            float u[2][3];
-            macro_cell<NC>(kp, nb, rd, slot, c, lx, ly, lz, held, u);
-        }
-        __syncthreads();
+        const uint32_t bits = cell_bits(kp, gid, c);
+        kp.nbits[(size_t)slot * CELLS + c] = bits;
+        const bool live = !(bits & 1u);
+        const unsigned fluid = __ballot_sync(FULL, live && !((bits >> HELD_BIT) & 1u));
+        if ((threadIdx.x & 31) == 0 && fluid)
+            atomicAdd(&ctrl->fluid_active, (unsigned long long)__popc(fluid));
+        const WarpNbr wn = warp_nbr(kp, gid, slot, n_old, true);
+        float rho[2], u[2][3];
+        macro_cell<NC>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, true, rho, u);
     }
 }
 
 // Forces on a fluid cell (Eqs. 8-9 as read, gravity, adhesion), from the
 // mac values of its 18 neighbours.  A solid neighbour lends the centre's own
-// values; an unmeshed one the ambient values.
+// values; an unmeshed one the ambient values.  All lanes must call.
 template <int NC>
-__device__ __forceinline__ void forces(const KParams &kp, const Nbr &nb, int slot, int c, int lx,
-                                       int ly, int lz, const float rho[2], float F[2][3])
+__device__ __forceinline__ void forces(const KParams &kp, const WarpNbr &wn, int slot, int c,
+                                       int lx, int ly, int lz, uint32_t bits, bool live,
+                                       const float rho[2], float F[2][3])
 {
-    const float *mc = kp.mac + (size_t)slot * MACS * CELLS;
-    const float psi_c = mc[CELLS + c];
+    const float psi_c = live ? kp.mac[(size_t)slot * CELLS + c].y : 0.f;
     const float r0c = rho[0], r1c = NC == 2 ? rho[1] : 0.f;
     float sp[3] = {0, 0, 0}, sp2[3] = {0, 0, 0}, sr0[3] = {0, 0, 0}, sr1[3] = {0, 0, 0},
           ss[3] = {0, 0, 0};
@@ -428,23 +508,25 @@ __device__ __forceinline__ void forces(const KParams &kp, const Nbr &nb, int slo
             constexpr int D = H == 0 ? I : J;
             const int tx = lx + cx(D), ty = ly + cy(D), tz = lz + cz(D);
             const int k = nbk(tx, ty, tz), lc = lcell(tx, ty, tz);
-            if (is_solid(nb, k, lc)) {
+            const int s = nb_slot(wn, k);
+            const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
+            const bool meshed = !solid_n && s >= 0;
+            const float4 *q = meshed ? kp.mac + (size_t)s * CELLS + lc : kp.mac + (size_t)slot * CELLS + c;
+            const float4 m = (live && meshed) ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (solid_n) {
                 psi_n[H] = psi_c;
                 r0_n[H] = r0c;
                 r1_n[H] = r1c;
                 s_n[H] = 1.f;
+            } else if (meshed) {
+                r0_n[H] = m.x;
+                psi_n[H] = m.y;
+                r1_n[H] = m.z;
+                s_n[H] = 0.f;
             } else {
-                const int s = nb.slot[k];
-                if (s >= 0) {
-                    const float *m = kp.mac + (size_t)s * MACS * CELLS + lc;
-                    r0_n[H] = m[0];
-                    psi_n[H] = m[CELLS];
-                    r1_n[H] = NC == 2 ? m[2 * CELLS] : 0.f;
-                } else {
-                    r0_n[H] = kp.rho_amb[0];
-                    psi_n[H] = kp.psi_amb;
-                    r1_n[H] = kp.rho_amb[1];
-                }
+                r0_n[H] = kp.rho_amb[0];
+                psi_n[H] = kp.psi_amb;
+                r1_n[H] = kp.rho_amb[1];
                 s_n[H] = 0.f;
             }
         });
@@ -487,81 +569,88 @@ __device__ __forceinline__ void forces(const KParams &kp, const Nbr &nb, int slo
 // 10-12, R1 sign), store into the other buffer; the velocity is kept for
 // the next criterion at cells that border unmeshed blocks.
 template <int NC, bool TAU1>
-__global__ void __launch_bounds__(CELLS) k_collide(KParams kp, int step)
+__global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
 {
-    __shared__ Nbr nb;
     Ctrl *ctrl = kp.ctrl;
     if (ctrl->status) return;
     const int par = step & 1;
     const int n = ctrl->n_active[par ^ 1];
     const float *rd = kp.f + (size_t)par * kp.buf_stride;
     float *wr = kp.f + (size_t)(par ^ 1) * kp.buf_stride;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->cell_updates += (unsigned long long)n * CELLS;
-    const int c = threadIdx.x, lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
-    const unsigned reach = reach_bits(lx, ly, lz);
-    for (int slot = blockIdx.x; slot < n; slot += gridDim.x) {
-        const int gid = kp.block_of[slot];
-        load_neighbourhood(kp, gid, slot, INT_MAX, nb);
-        if (threadIdx.x == 0) {
-            int nf = 0;
-            for (int w = 0; w < MASK_WORDS; ++w) nf += __popc(~(nb.solid[13][w] | nb.held[w]));
-            atomicAdd(&ctrl->fluid_updates, (unsigned long long)nf);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->cell_updates += (unsigned long long)n * CELLS;
+        ctrl->fluid_updates += ctrl->fluid_active;
+    }
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
-        const bool solid = is_solid(nb, 13, c);
-        const bool held = (nb.held[c >> 5] >> (c & 31)) & 1u;
-        if (!solid && !held) {
-            float fin[NC][Q], rho[2] = {0.f, 0.f}, u[2][3];
+        const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+        Moments m;
+        float fin[TAU1 ? 1 : NC][Q];
+        pull<NC>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, [&]<int I>(int a, float v) {
+            m.template add<I>(a, v);
+            if constexpr (!TAU1) fin[a][I] = v;
+        });
+        float rho[2] = {m.rho[0], m.rho[1]}, u[2][3];
 #pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                float j[3];
-                pull(kp, nb, rd, slot, a, c, lx, ly, lz, false, fin[a]);
-                moments(fin[a], rho[a], j);
-                const float inv = 1.f / rho[a];
-                u[a][0] = j[0] * inv;
-                u[a][1] = j[1] * inv;
-                u[a][2] = j[2] * inv;
-            }
-            float F[2][3];
-            forces<NC>(kp, nb, slot, c, lx, ly, lz, rho, F);
+        for (int a = 0; a < NC; ++a) {
+            const float inv = 1.f / rho[a];
+            u[a][0] = m.j[a][0] * inv;
+            u[a][1] = m.j[a][1] * inv;
+            u[a][2] = m.j[a][2] * inv;
+        }
+        float F[2][3];
+        forces<NC>(kp, wn, slot, c, lx, ly, lz, bits, live, rho, F);
+        if (!live) continue;
 #pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const float inv = 1.f / rho[a];
-                const float vx = u[a][0] + F[a][0] * inv, vy = u[a][1] + F[a][1] * inv,
-                            vz = u[a][2] + F[a][2] * inv;
-                const float vv = vx * vx + vy * vy + vz * vz;
-                const float uu = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
-                float *dst = wr + (size_t)slot * kp.slot_floats + a * Q * CELLS + c;
-                const float r = rho[a];
-                // The 18 moving populations from Eqs. 10-12; the rest
-                // population from the mass balance sum_i f_i = rho, which
-                // the collision satisfies exactly in real arithmetic.  In
-                // FP32 this keeps the mass free of the systematic bias of
-                // the rounded weights (fl(1/3) + 6 fl(1/18) + 12 fl(1/36)
-                // = 1 + 1.5e-8).
-                float moving = 0.f;
-                Unroll<1, Q>::run([&]<int I>() {
-                    const float wr_ = wgt(I) * r;
-                    float v = feq<I>(wr_, vx, vy, vz, vv);
-                    if (!TAU1) {
-                        const float e0 = feq<I>(wr_, u[a][0], u[a][1], u[a][2], uu);
-                        v += (1.f - kp.omega) * (fin[a][I] - e0);
-                    }
-                    moving += v;
-                    dst[I * CELLS] = v;
-                });
-                dst[0] = r - moving;
-            }
-            if (kp.progressive && (reach & nb.amb_bits)) {
-#pragma unroll
-                for (int a = 0; a < NC; ++a) {
-                    float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
-                    up[0] = u[a][0];
-                    up[CELLS] = u[a][1];
-                    up[2 * CELLS] = u[a][2];
+        for (int a = 0; a < NC; ++a) {
+            const float inv = 1.f / rho[a];
+            const float vx = u[a][0] + F[a][0] * inv, vy = u[a][1] + F[a][1] * inv,
+                        vz = u[a][2] + F[a][2] * inv;
+            const float vv = vx * vx + vy * vy + vz * vz;
+            const float uu = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
+            float *dst = wr + (size_t)slot * kp.slot_floats + a * Q * CELLS + c;
+            const float r = rho[a];
+            // The 18 moving populations from Eqs. 10-12; the rest population
+            // from the mass balance sum_i f_i = rho, which the collision
+            // satisfies exactly in real arithmetic.  In FP32 this keeps the
+            // mass free of the systematic bias of the rounded weights
+            // (fl(1/3) + 6 fl(1/18) + 12 fl(1/36) = 1 + 1.5e-8).
+            float moving = 0.f;
+            Unroll<1, Q>::run([&]<int I>() {
+                const float wr_ = wgt(I) * r;
+                float v = feq<I>(wr_, vx, vy, vz, vv);
+                if constexpr (!TAU1) {
+                    const float e0 = feq<I>(wr_, u[a][0], u[a][1], u[a][2], uu);
+                    v += (1.f - kp.omega) * (fin[a][I] - e0);
                 }
+                moving += v;
+                dst[I * CELLS] = v;
+            });
+            dst[0] = r - moving;
+        }
+        if (kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+                up[0] = u[a][0];
+                up[CELLS] = u[a][1];
+                up[2 * CELLS] = u[a][2];
             }
         }
-        __syncthreads();
     }
 }
 
@@ -569,40 +658,35 @@ __global__ void __launch_bounds__(CELLS) k_collide(KParams kp, int step)
 // out[slot - slot0][4][CELLS] = rho, ux, uy, uz, velocity u + F / (2 rho)
 // at fluid cells (R9), own moments at held cells, zeros at solid cells.
 template <int NC>
-__global__ void __launch_bounds__(CELLS) k_output(KParams kp, int rdbuf, int comp, int slot0,
-                                                  int nslots, float *out)
+__global__ void __launch_bounds__(THREADS) k_output(KParams kp, int rdbuf, int comp, int slot0,
+                                                    int nslots, float *out)
 {
-    __shared__ Nbr nb;
     const float *rd = kp.f + (size_t)rdbuf * kp.buf_stride;
-    const int c = threadIdx.x, lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
-    for (int r = blockIdx.x; r < nslots; r += gridDim.x) {
+    for (int it = blockIdx.x; it < nslots * PARTS; it += gridDim.x) {
+        const int r = it / PARTS;
         const int slot = slot0 + r;
-        const int gid = kp.block_of[slot];
-        load_neighbourhood(kp, gid, slot, INT_MAX, nb);
-        const bool solid = is_solid(nb, 13, c);
-        const bool held = (nb.held[c >> 5] >> (c & 31)) & 1u;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(nbr_row_lane(kp, slot));
+        const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+        const bool live = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        Moments m;
+        pull<NC>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false,
+                 [&]<int I>(int a, float v) { m.template add<I>(a, v); });
+        float rho[2] = {m.rho[0], m.rho[1]};
+        float F[2][3];
+        forces<NC>(kp, wn, slot, c, lx, ly, lz, bits, live && !held, rho, F);
         float o[4] = {0.f, 0.f, 0.f, 0.f};
-        if (!solid) {
-            float rho[2] = {0.f, 0.f}, u[2][3];
-#pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                float fin[Q], j[3];
-                pull(kp, nb, rd, slot, a, c, lx, ly, lz, held, fin);
-                moments(fin, rho[a], j);
-                const float inv = 1.f / rho[a];
-                u[a][0] = j[0] * inv;
-                u[a][1] = j[1] * inv;
-                u[a][2] = j[2] * inv;
-            }
+        if (live) {
             const int a = comp;
+            const float inv = 1.f / rho[a];
             o[0] = rho[a];
-            o[1] = u[a][0];
-            o[2] = u[a][1];
-            o[3] = u[a][2];
+            o[1] = m.j[a][0] * inv;
+            o[2] = m.j[a][1] * inv;
+            o[3] = m.j[a][2] * inv;
             if (!held) {
-                float F[2][3];
-                forces<NC>(kp, nb, slot, c, lx, ly, lz, rho, F);
-                const float h = 0.5f / rho[a];
+                const float h = 0.5f * inv;
                 o[1] += F[a][0] * h;
                 o[2] += F[a][1] * h;
                 o[3] += F[a][2] * h;
@@ -610,8 +694,7 @@ __global__ void __launch_bounds__(CELLS) k_output(KParams kp, int rdbuf, int com
         }
         float *dst = out + (size_t)r * 4 * CELLS + c;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) dst[m * CELLS] = o[m];
-        __syncthreads();
+        for (int q = 0; q < 4; ++q) dst[q * CELLS] = o[q];
     }
 }
 
@@ -624,8 +707,7 @@ __global__ void __launch_bounds__(CELLS) k_mass_partial(KParams kp, int rdbuf, i
     const float *rd = kp.f + (size_t)rdbuf * kp.buf_stride;
     const int c = threadIdx.x;
     for (int slot = blockIdx.x; slot < n; slot += gridDim.x) {
-        const int gid = kp.block_of[slot];
-        const bool solid = (kp.solid[(size_t)gid * MASK_WORDS + (c >> 5)] >> (c & 31)) & 1u;
+        const bool solid = kp.nbits[(size_t)slot * CELLS + c] & 1u;
         double m[2] = {0.0, 0.0};
         for (int a = 0; a < kp.ncomp; ++a) {
             if (solid) continue;
@@ -636,7 +718,7 @@ __global__ void __launch_bounds__(CELLS) k_mass_partial(KParams kp, int rdbuf, i
             m[a] = acc;
         }
         for (int a = 0; a < 2; ++a)
-            for (int o = 16; o > 0; o >>= 1) m[a] += __shfl_down_sync(0xffffffffu, m[a], o);
+            for (int o = 16; o > 0; o >>= 1) m[a] += __shfl_down_sync(FULL, m[a], o);
         if ((c & 31) == 0) {
             red[c >> 5][0] = m[0];
             red[c >> 5][1] = m[1];
@@ -691,46 +773,61 @@ cudaError_t launch_ambient_psi(const KParams &kp, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro(const KParams &kp, int step, int criterion, int grid, cudaStream_t s)
+// Resident CTAs per SM of a kernel, looked up once per process.
+template <class K>
+int occupancy(K kernel)
 {
-    if (kp.ncomp == 2)
-        k_macro<2><<<grid, CELLS, 0, s>>>(kp, step, criterion);
-    else
-        k_macro<1><<<grid, CELLS, 0, s>>>(kp, step, criterion);
+    static int cached = 0;
+    if (!cached) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, THREADS, 0) != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+        }
+        cached = n > 0 ? n : 1;
+    }
+    return cached;
+}
+
+template <class K, class... A>
+cudaError_t launch_persistent(K kernel, int sms, cudaStream_t s, A... args)
+{
+    kernel<<<sms * occupancy(kernel), THREADS, 0, s>>>(args...);
     return cudaGetLastError();
 }
 
-cudaError_t launch_activate(const KParams &kp, int step, int grid, cudaStream_t s)
+cudaError_t launch_macro(const KParams &kp, int step, int criterion, int sms, cudaStream_t s)
+{
+    if (kp.ncomp == 2) return launch_persistent(k_macro<2>, sms, s, kp, step, criterion);
+    return launch_persistent(k_macro<1>, sms, s, kp, step, criterion);
+}
+
+cudaError_t launch_activate(const KParams &kp, int step, int sms, cudaStream_t s)
 {
     if (kp.ncomp == 2)
-        k_activate<2><<<grid, CELLS, 0, s>>>(kp, step);
+        k_activate<2><<<sms, THREADS, 0, s>>>(kp, step);
     else
-        k_activate<1><<<grid, CELLS, 0, s>>>(kp, step);
+        k_activate<1><<<sms, THREADS, 0, s>>>(kp, step);
     return cudaGetLastError();
 }
 
-cudaError_t launch_collide(const KParams &kp, int step, int grid, cudaStream_t s)
+cudaError_t launch_collide(const KParams &kp, int step, int sms, cudaStream_t s)
 {
     const bool tau1 = kp.omega == 1.0f;
     if (kp.ncomp == 2) {
-        if (tau1) k_collide<2, true><<<grid, CELLS, 0, s>>>(kp, step);
-        else k_collide<2, false><<<grid, CELLS, 0, s>>>(kp, step);
-    } else {
-        if (tau1) k_collide<1, true><<<grid, CELLS, 0, s>>>(kp, step);
-        else k_collide<1, false><<<grid, CELLS, 0, s>>>(kp, step);
+        if (tau1) return launch_persistent(k_collide<2, true>, sms, s, kp, step);
+        return launch_persistent(k_collide<2, false>, sms, s, kp, step);
     }
-    return cudaGetLastError();
+    if (tau1) return launch_persistent(k_collide<1, true>, sms, s, kp, step);
+    return launch_persistent(k_collide<1, false>, sms, s, kp, step);
 }
 
 cudaError_t launch_output(const KParams &kp, int rd, int comp, int slot0, int nslots, float *out,
-                          int grid, cudaStream_t s)
+                          int sms, cudaStream_t s)
 {
     if (nslots <= 0) return cudaSuccess;
-    if (kp.ncomp == 2)
-        k_output<2><<<grid, CELLS, 0, s>>>(kp, rd, comp, slot0, nslots, out);
-    else
-        k_output<1><<<grid, CELLS, 0, s>>>(kp, rd, comp, slot0, nslots, out);
-    return cudaGetLastError();
+    if (kp.ncomp == 2) return launch_persistent(k_output<2>, sms, s, kp, rd, comp, slot0, nslots, out);
+    return launch_persistent(k_output<1>, sms, s, kp, rd, comp, slot0, nslots, out);
 }
 
 cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, double *out, int grid,
@@ -747,10 +844,13 @@ cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, doubl
 
 int max_ctas_per_sm_stream_kernels()
 {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide<2, true>, CELLS, 0) !=
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_collide<2, true>, THREADS, 0) !=
         cudaSuccess)
         return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_macro<2>, THREADS, 0) != cudaSuccess)
+        return 1;
+    const int n = a < b ? a : b;
     return n > 0 ? n : 1;
 }
 
