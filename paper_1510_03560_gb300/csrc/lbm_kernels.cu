@@ -202,34 +202,43 @@ __device__ __forceinline__ void pull(const KParams &kp, const WarpNbr &wn, const
                                      int own_slot, int c, int lx, int ly, int lz, uint32_t bits,
                                      bool live, bool own_ambient, Sink &&sink)
 {
-    const float *own = rd + (size_t)own_slot * kp.slot_floats + c;
+    const uint32_t own = (uint32_t)own_slot * (uint32_t)kp.slot_floats + (uint32_t)c;
     const bool held = (bits >> HELD_BIT) & 1u;
-    // Every population is one unconditional (predicated) load from an address
-    // chosen without branching, so that all of a cell's loads can be in
-    // flight together; the ambient value replaces the loaded one afterwards.
-    auto one = [&]<int I>() {
+    // Three phases, so that all of a cell's loads are in flight together:
+    // (1) the source offset of every population (32-bit, from the read
+    // buffer; one shuffle each) and which ones take the ambient value,
+    // (2) every load, unconditional but for dead lanes, (3) the sink.
+    uint32_t off[Q];
+    uint32_t amb = 0;
+    Unroll<0, Q>::run([&]<int I>() {
         const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
         const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
         const int s = nb_slot(wn, k);
         const bool bounce = (bits >> I) & 1u;
-        bool from_nb, amb;
-        const float *p;
+        bool from_nb, a;
         if (own_ambient) {
             from_nb = s >= 0 && !bounce;
-            amb = !from_nb;
-            p = from_nb ? rd + (size_t)s * kp.slot_floats + I * CELLS + lc : own + I * CELLS;
+            a = !from_nb;
         } else {
             from_nb = !held && !bounce && s >= 0;
-            amb = !held && !bounce && s < 0;
-            p = from_nb ? rd + (size_t)s * kp.slot_floats + I * CELLS + lc
-                        : own + ((held || amb) ? I : opp(I)) * CELLS;
+            a = !held && !bounce && s < 0;
         }
-        const bool load = live && !amb;
+        off[I] = from_nb ? (uint32_t)s * (uint32_t)kp.slot_floats + (uint32_t)(I * CELLS + lc)
+                         : own + (uint32_t)(((held || a) ? I : opp(I)) * CELLS);
+        amb |= (uint32_t)a << I;
+    });
+    float v[NC][Q];
+    Unroll<0, Q>::run([&]<int I>() {
+        const bool a = (amb >> I) & 1u;
 #pragma unroll
-        for (int a = 0; a < NC; ++a) {
-            float v = load ? __ldg(p + a * Q * CELLS) : 0.f;
-            if (live && amb) v = kp.famb[a][I];
-            sink.template operator()<I>(a, v);
+        for (int c2 = 0; c2 < NC; ++c2)
+            v[c2][I] = (live && !a) ? __ldg(rd + off[I] + c2 * Q * CELLS) : 0.f;
+    });
+    auto one = [&]<int I>() {
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) {
+            const float x = (live && ((amb >> I) & 1u)) ? kp.famb[c2][I] : v[c2][I];
+            sink.template operator()<I>(c2, x);
         }
     };
     one.template operator()<0>();
