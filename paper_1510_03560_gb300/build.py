@@ -36,17 +36,23 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
+def build(verbose: bool = False, force: bool = False, checked: bool = False) -> str:
+    """Build liblbm.so; with checked=True build liblbm_checked.so instead, whose
+    step kernels test every slot and cell index before use and report the
+    first failure through lbm_step's error (a debugging aid)."""
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     objs, jobs = [], []
+    suffix = "_checked" if checked else ""
+    lib = LIB.replace(".so", suffix + ".so")
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src + ".o")
+        o = os.path.join(BUILD, src + suffix + ".o")
         objs.append(o)
         if force or _stale(o, [s, *HEADERS]):
             extra = ["-x", "cu"] if src.endswith(".cu") else []
-            jobs.append([nvcc, *_flags(), *extra, "-c", s, "-o", o])
+            defs = ["-DLBM_CHECKED"] if checked else []
+            jobs.append([nvcc, *_flags(), *defs, *extra, "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -58,11 +64,11 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -284,6 +284,11 @@ int finish(lbm_ctx *c)
     int rc = read_ctrl(c, ctrl);
     if (rc) return rc;
     if (c->profiling) flush_profile(c);
+    if (ctrl.check_site != 0) {
+        c->sticky = LBM_ECUDA;
+        return fail(c, LBM_ECUDA, "device index check %d failed (value %lld)", ctrl.check_site,
+                    ctrl.check_value);
+    }
     if (ctrl.status != 0) {
         c->step = ctrl.fail_step;
         c->sticky = ctrl.status;

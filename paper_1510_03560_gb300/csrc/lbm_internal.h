@@ -32,7 +32,8 @@ struct Ctrl {
     unsigned long long fluid_updates;  // fluid cells of meshed blocks, summed over steps
     unsigned long long fluid_active;   // fluid cells of the meshed blocks now
     float psi_amb;     // psi of the ambient density, evaluated on the device
-    int pad;
+    int check_site;    // checked builds: first failed index check (site id)
+    long long check_value;  // and the offending value
 };
 
 // Everything a kernel needs, passed by value.

@@ -36,6 +36,21 @@ namespace lbm {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// Checked builds (-DLBM_CHECKED) test the slot and block indices of the step
+// kernels before use; a failure records the site and value in the control
+// words (lbm_step then fails) and the access is skipped.  Normal builds
+// compile the checks away.
+#ifdef LBM_CHECKED
+__device__ __forceinline__ bool in_range(const KParams &kp, long long v, long long hi, int site)
+{
+    if (v >= 0 && v < hi) return true;
+    if (atomicCAS(&kp.ctrl->check_site, 0, site) == 0) kp.ctrl->check_value = v;
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_range(const KParams &, long long, long long, int) { return true; }
+#endif
 constexpr int THREADS = 256;            // threads per CTA of the cell kernels
 constexpr int PARTS = CELLS / THREADS;  // CTA work items per block
 
@@ -370,6 +385,7 @@ __global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int cri
     if (criterion && ctrl->status) return;
     const int par = step & 1;
     const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
     const float *rd = kp.f + (size_t)par * kp.buf_stride;
     const int lane = threadIdx.x & 31;
     const int total = n * PARTS;
@@ -392,6 +408,8 @@ __global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int cri
         }
         const bool live = !(bits & 1u);
         const bool held = (bits >> HELD_BIT) & 1u;
+        // (warp-uniform: the pull below shuffles)
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
         float rho[2], u[2][3];
         macro_cell<NC>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, rho, u);
         if (criterion) {
@@ -413,7 +431,8 @@ __global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int cri
                 // a candidate takes the next slot after the meshed ones now
                 // (k_activate checks the capacity and undoes it if full)
                 const int nid = neighbour_of(kp, kp.block_of[slot], lane);
-                if (atomicCAS(&kp.cand_mark[nid], 0u, 1u) == 0u) {
+                if (in_range(kp, nid, (long long)kp.nbx * kp.nby * kp.nbz, 3) &&
+                    atomicCAS(&kp.cand_mark[nid], 0u, 1u) == 0u) {
                     const int pos = atomicAdd(&ctrl->ncand[par], 1);
                     kp.cand_list[pos] = nid;
                     if (n + pos < kp.capacity) kp.slot_of[nid] = n + pos;
@@ -435,6 +454,7 @@ __global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
     const int par = step & 1;
     const int n_old = ctrl->n_active[par];
     const int ncand = ctrl->ncand[par];
+    if (!in_range(kp, ncand, (long long)kp.nbx * kp.nby * kp.nbz + 1, 4)) return;
     if (n_old + ncand > kp.capacity) {
         // the pool cannot hold them: undo the slots k_macro handed out, so
         // the state stays that of the last completed step
@@ -460,6 +480,7 @@ __global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
         const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
         const int slot = n_old + k;
         const int gid = kp.cand_list[k];
+        if (!in_range(kp, gid, (long long)kp.nbx * kp.nby * kp.nbz, 5)) continue;
         if (c == 0) kp.block_of[slot] = gid;
         if (c < 32) {
             // the new block's row of the neighbour-slot table, and its slot in
@@ -471,7 +492,8 @@ __global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
             } else if (c < 27) {
                 const int nid = neighbour_of(kp, gid, c);
                 if (nid >= 0) s = kp.slot_of[nid];
-                if (s >= 0) kp.nbr[(size_t)s * NBR_STRIDE + (26 - c)] = slot;
+                if (s >= 0 && in_range(kp, s, kp.capacity, 6))
+                    kp.nbr[(size_t)s * NBR_STRIDE + (26 - c)] = slot;
             }
             kp.nbr[(size_t)slot * NBR_STRIDE + c] = s;
         }
@@ -584,6 +606,7 @@ __global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
     if (ctrl->status) return;
     const int par = step & 1;
     const int n = ctrl->n_active[par ^ 1];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 7)) return;
     const float *rd = kp.f + (size_t)par * kp.buf_stride;
     float *wr = kp.f + (size_t)(par ^ 1) * kp.buf_stride;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -607,6 +630,7 @@ __global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
             next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
         const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) continue;
         Moments m;
         float fin[TAU1 ? 1 : NC][Q];
         pull<NC>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, [&]<int I>(int a, float v) {

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "liblbm.so")
+# LBM_CHECKED=1 selects the bounds-checked debug build (build(checked=True))
+LIB_PATH = os.path.join(_PKG, "liblbm_checked.so" if os.environ.get("LBM_CHECKED") == "1"
+                        else "liblbm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, 1, 2, 3, 4
 Q = 19
