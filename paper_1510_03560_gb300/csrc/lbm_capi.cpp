@@ -350,13 +350,18 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
     const size_t slot_floats = (size_t)p->ncomp * Q * CELLS;
     KParams &k = c->kp;
     k.slot_floats = (int)slot_floats;
-    k.buf_stride = slot_floats * (size_t)c->capacity;
+    k.amb_slot = c->capacity;
+    k.buf_stride = slot_floats * (size_t)(c->capacity + 1);
+    if (k.buf_stride >= (1ull << 32)) {
+        fail(c, LBM_EINVAL, "block pool of %d blocks too large for 32-bit offsets", c->capacity);
+        return bail(LBM_EINVAL);
+    }
     struct Want {
         void **dst;
         size_t bytes;
     } want[] = {
         {(void **)&k.f, 2 * k.buf_stride * sizeof(float)},
-        {(void **)&k.mac, (size_t)c->capacity * CELLS * sizeof(float4)},
+        {(void **)&k.mac, (size_t)(c->capacity + 1) * CELLS * sizeof(float4)},
         {(void **)&k.nbits, (size_t)c->capacity * CELLS * sizeof(uint32_t)},
         {(void **)&k.nbr, (size_t)c->capacity * NBR_STRIDE * sizeof(int)},
         {(void **)&k.uprev, p->progressive ? (size_t)c->capacity * p->ncomp * 3 * CELLS * sizeof(float) : 0},
@@ -514,7 +519,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     Ctrl ctrl{};
     ctrl.n_active[0] = ctrl.n_active[1] = n0;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(k.ctrl, &ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
-    CUDA_OR_FAIL(c, launch_ambient_psi(k, s));
+    CUDA_OR_FAIL(c, launch_ambient_slot(k, s));
     float psi_amb = 0.f;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(&psi_amb, &k.ctrl->psi_amb, sizeof(float), cudaMemcpyDeviceToHost, s));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(s));

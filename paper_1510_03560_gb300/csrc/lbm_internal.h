@@ -42,6 +42,8 @@ struct KParams {
     int per[3];
     int ncomp;
     int capacity;
+    int amb_slot;       // == capacity: a slot holding the resting ambient state
+                        // (populations in both buffers, first-pass values)
     int progressive;
     // physics, FP32
     float omega;        // 1 / tau
@@ -56,8 +58,8 @@ struct KParams {
     float psi_amb;
     float famb[2][Q];   // ambient resting populations w_i rho_amb
     // device memory
-    float *f;           // [2][capacity][ncomp][Q][CELLS]
-    float4 *mac;        // [capacity][CELLS]: rho0, psi0, rho1, 0 of the current step
+    float *f;           // [2][capacity + 1][ncomp][Q][CELLS]
+    float4 *mac;        // [capacity + 1][CELLS]: rho0, psi0, rho1, 0 of the current step
     uint32_t *nbits;    // [capacity][CELLS]: bit i set when cell x - e_i is solid
                         // (bit 0: the cell itself), bit HELD_BIT: held cell
     float *uprev;       // [capacity][ncomp][3][CELLS]
@@ -80,7 +82,7 @@ enum KernelKind { K_MACRO = 0, K_ACTIVATE = 1, K_COLLIDE = 2, K_OTHER = 3 };
 // launch status.
 cudaError_t launch_init(const KParams &kp, const float *in_block, int slot0, int nslots,
                         int grid, cudaStream_t s);
-cudaError_t launch_ambient_psi(const KParams &kp, cudaStream_t s);
+cudaError_t launch_ambient_slot(const KParams &kp, cudaStream_t s);
 // The cell kernels size their persistent grids themselves: `sms` x the
 // CTAs per SM their occupancy allows.
 cudaError_t launch_macro(const KParams &kp, int step, int criterion, int sms, cudaStream_t s);

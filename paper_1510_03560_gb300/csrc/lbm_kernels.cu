@@ -142,9 +142,19 @@ __device__ __forceinline__ int neighbour_of(const KParams &kp, int gid, int k)
 // warp-uniform mask of unmeshed neighbours.  Slots >= slot_limit count as
 // unmeshed.  Every lane of the warp calls it.
 struct WarpNbr {
-    int slot;
-    unsigned amb;
+    int slot;         // slot, AMBIENT or SOLIDBLK
+    unsigned amb;     // warp-uniform: bit k set when neighbour k is unmeshed
+    uint32_t fbase;   // population offset of the slot (the ambient slot for
+                      // unmeshed or solid blocks)
+    uint32_t mbase;   // first-pass value offset, likewise
 };
+
+__device__ __forceinline__ WarpNbr make_nbr(const KParams &kp, int s)
+{
+    const uint32_t q = s >= 0 ? (uint32_t)s : (uint32_t)kp.amb_slot;
+    return WarpNbr{s, __ballot_sync(FULL, s == AMBIENT) & ~(1u << 13), q * (uint32_t)kp.slot_floats,
+                   q * (uint32_t)CELLS};
+}
 
 __device__ __forceinline__ WarpNbr warp_nbr(const KParams &kp, int gid, int own_slot, int slot_limit,
                                             bool own_unmeshed = false)
@@ -160,7 +170,7 @@ __device__ __forceinline__ WarpNbr warp_nbr(const KParams &kp, int gid, int own_
             if (s >= slot_limit) s = AMBIENT;
         }
     }
-    return WarpNbr{s, __ballot_sync(FULL, s == AMBIENT) & ~(1u << 13)};
+    return make_nbr(kp, s);
 }
 
 // The same, read from the slot's row of the neighbour-slot table (kept up to
@@ -169,12 +179,12 @@ __device__ __forceinline__ int nbr_row_lane(const KParams &kp, int slot)
 {
     return kp.nbr[(size_t)slot * NBR_STRIDE + (threadIdx.x & 31)];
 }
-__device__ __forceinline__ WarpNbr warp_nbr_of(int lane_slot)
+__device__ __forceinline__ WarpNbr warp_nbr_of(const KParams &kp, int lane_slot)
 {
-    return WarpNbr{lane_slot, __ballot_sync(FULL, lane_slot == AMBIENT) & ~(1u << 13)};
+    return make_nbr(kp, lane_slot);
 }
 
-__device__ __forceinline__ int nb_slot(const WarpNbr &w, int k) { return __shfl_sync(FULL, w.slot, k); }
+
 
 // Neighbour blocks reachable from a cell through the 18 moving velocities.
 __device__ __forceinline__ unsigned reach_bits(int lx, int ly, int lz)
@@ -217,43 +227,31 @@ __device__ __forceinline__ void pull(const KParams &kp, const WarpNbr &wn, const
                                      int own_slot, int c, int lx, int ly, int lz, uint32_t bits,
                                      bool live, bool own_ambient, Sink &&sink)
 {
-    const uint32_t own = (uint32_t)own_slot * (uint32_t)kp.slot_floats + (uint32_t)c;
+    const uint32_t own =
+        (own_ambient ? (uint32_t)kp.amb_slot : (uint32_t)own_slot) * (uint32_t)kp.slot_floats + (uint32_t)c;
     const bool held = (bits >> HELD_BIT) & 1u;
     // Three phases, so that all of a cell's loads are in flight together:
     // (1) the source offset of every population (32-bit, from the read
-    // buffer; one shuffle each) and which ones take the ambient value,
-    // (2) every load, unconditional but for dead lanes, (3) the sink.
+    // buffer; one shuffle each: unmeshed blocks read the ambient slot),
+    // (2) every load, (3) the sink.
     uint32_t off[Q];
-    uint32_t amb = 0;
     Unroll<0, Q>::run([&]<int I>() {
         const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
         const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
-        const int s = nb_slot(wn, k);
+        const uint32_t base = __shfl_sync(FULL, wn.fbase, k);
         const bool bounce = (bits >> I) & 1u;
-        bool from_nb, a;
-        if (own_ambient) {
-            from_nb = s >= 0 && !bounce;
-            a = !from_nb;
-        } else {
-            from_nb = !held && !bounce && s >= 0;
-            a = !held && !bounce && s < 0;
-        }
-        off[I] = from_nb ? (uint32_t)s * (uint32_t)kp.slot_floats + (uint32_t)(I * CELLS + lc)
-                         : own + (uint32_t)(((held || a) ? I : opp(I)) * CELLS);
-        amb |= (uint32_t)a << I;
+        off[I] = held ? own + (uint32_t)(I * CELLS)
+                      : (bounce ? own + (uint32_t)(opp(I) * CELLS) : base + (uint32_t)(I * CELLS + lc));
     });
     float v[NC][Q];
     Unroll<0, Q>::run([&]<int I>() {
-        const bool a = (amb >> I) & 1u;
 #pragma unroll
-        for (int c2 = 0; c2 < NC; ++c2)
-            v[c2][I] = (live && !a) ? __ldg(rd + off[I] + c2 * Q * CELLS) : 0.f;
+        for (int c2 = 0; c2 < NC; ++c2) v[c2][I] = live ? __ldg(rd + off[I] + c2 * Q * CELLS) : 0.f;
     });
     auto one = [&]<int I>() {
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) {
-            const float x = (live && ((amb >> I) & 1u)) ? kp.famb[c2][I] : v[c2][I];
-            sink.template operator()<I>(c2, x);
+            sink.template operator()<I>(c2, v[c2][I]);
         }
     };
     one.template operator()<0>();
@@ -348,9 +346,22 @@ __global__ void __launch_bounds__(CELLS) k_init(KParams kp, const float *in, int
     }
 }
 
-__global__ void k_ambient_psi(KParams kp)
+// The ambient slot: resting ambient populations in both buffers and the
+// ambient first-pass values, read wherever a neighbour block is unmeshed.
+__global__ void __launch_bounds__(CELLS) k_ambient_slot(KParams kp)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) kp.ctrl->psi_amb = psi_of(kp, kp.rho_amb[0]);
+    const int c = threadIdx.x;
+    const float psi = psi_of(kp, kp.rho_amb[0]);
+    if (c == 0) kp.ctrl->psi_amb = psi;
+    for (int a = 0; a < kp.ncomp; ++a) {
+        float *d0 = kp.f + (size_t)kp.amb_slot * kp.slot_floats + a * Q * CELLS + c;
+        float *d1 = d0 + kp.buf_stride;
+        for (int i = 0; i < Q; ++i) {
+            d0[i * CELLS] = kp.famb[a][i];
+            d1[i * CELLS] = kp.famb[a][i];
+        }
+    }
+    kp.mac[(size_t)kp.amb_slot * CELLS + c] = make_float4(kp.rho_amb[0], psi, kp.rho_amb[1], 0.f);
 }
 
 // Streaming + moments of one cell; writes mac (live cells), returns rho and
@@ -399,7 +410,7 @@ __global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int cri
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
         const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
-        const WarpNbr wn = warp_nbr_of(next_row);
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
         if (it2 < total) {
@@ -539,27 +550,13 @@ __device__ __forceinline__ void forces(const KParams &kp, const WarpNbr &wn, int
             constexpr int D = H == 0 ? I : J;
             const int tx = lx + cx(D), ty = ly + cy(D), tz = lz + cz(D);
             const int k = nbk(tx, ty, tz), lc = lcell(tx, ty, tz);
-            const int s = nb_slot(wn, k);
+            const uint32_t mb = __shfl_sync(FULL, wn.mbase, k);
             const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
-            const bool meshed = !solid_n && s >= 0;
-            const float4 *q = meshed ? kp.mac + (size_t)s * CELLS + lc : kp.mac + (size_t)slot * CELLS + c;
-            const float4 m = (live && meshed) ? __ldg(q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (solid_n) {
-                psi_n[H] = psi_c;
-                r0_n[H] = r0c;
-                r1_n[H] = r1c;
-                s_n[H] = 1.f;
-            } else if (meshed) {
-                r0_n[H] = m.x;
-                psi_n[H] = m.y;
-                r1_n[H] = m.z;
-                s_n[H] = 0.f;
-            } else {
-                r0_n[H] = kp.rho_amb[0];
-                psi_n[H] = kp.psi_amb;
-                r1_n[H] = kp.rho_amb[1];
-                s_n[H] = 0.f;
-            }
+            const float4 m = live ? __ldg(kp.mac + mb + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
+            psi_n[H] = solid_n ? psi_c : m.y;
+            r0_n[H] = solid_n ? r0c : m.x;
+            r1_n[H] = solid_n ? r1c : m.z;
+            s_n[H] = solid_n ? 1.f : 0.f;
         });
         const float w = wgt(I);
         const float dp = w * (psi_n[0] - psi_n[1]);
@@ -622,7 +619,7 @@ __global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
         const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
-        const WarpNbr wn = warp_nbr_of(next_row);
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
         if (it2 < total) {
@@ -700,7 +697,7 @@ __global__ void __launch_bounds__(THREADS) k_output(KParams kp, int rdbuf, int c
         const int slot = slot0 + r;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
         const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
-        const WarpNbr wn = warp_nbr_of(nbr_row_lane(kp, slot));
+        const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
         const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
         const bool live = !(bits & 1u);
         const bool held = (bits >> HELD_BIT) & 1u;
@@ -800,9 +797,9 @@ cudaError_t launch_init(const KParams &kp, const float *in_block, int slot0, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_ambient_psi(const KParams &kp, cudaStream_t s)
+cudaError_t launch_ambient_slot(const KParams &kp, cudaStream_t s)
 {
-    k_ambient_psi<<<1, 32, 0, s>>>(kp);
+    k_ambient_slot<<<1, CELLS, 0, s>>>(kp);
     return cudaGetLastError();
 }
 
