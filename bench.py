@@ -31,7 +31,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "active-cell MLUPS (D3Q19, 2 comp) & % HBM roofline vs static mesh, same GPU"
-BYTES_PER_UPDATE = 304  # FP32: 2 components x 19 populations x 4 B, read + write
+# algorithmic bytes per fluid-cell update: 2 components x 19 populations,
+# read + write, 4 B each (FP32 storage) or 2 B (16-bit deviation storage)
+BYTES_PER_UPDATE = {"fp32": 304, "fp16": 152, "bf16": 152}
 WORKLOAD = ("porous injection 256^3 (seeded spheres r 6-12, solid 0.30, 64^2 inlet u=0.02, "
             "g_ads=-0.2, 2 components), 5000 steps, 8^3 blocks")
 CPU_SAMPLE = "64^3 crop of the same recipe (seed 1510035603, 16^2 inlet), progressive mesh"
@@ -46,17 +48,18 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_traffic():
-    """ncu DRAM bytes per meshed cell of the force+collide kernel, if the
-    committed capture was taken on the current kernel source."""
+def kernel_traffic(storage):
+    """ncu DRAM bytes per meshed cell of the force+collide kernel in one
+    storage form, if the committed capture was taken on the current kernel
+    source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1510_03560_gb300", "csrc", "lbm_kernels.cu")
+    src = os.path.join(ROOT, "paper_1510_03560_gb300", "csrc", "lbm_step.cuh")
     try:
         with open(path) as fh:
             d = json.load(fh)
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if d.get("kernels_sha256") == h:
-            return float(d["collide_dram_bytes_per_cell"])
+            return float(d["forms"][storage]["collide_dram_bytes_per_cell"])
     except Exception:
         pass
     return None
@@ -135,9 +138,9 @@ def make_case(S=None, size=256):
     return W.porous_injection(**kw)
 
 
-def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid):
+def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32"):
     """Warm up, then time `steps` steps one by one (L2 flushed before each)."""
-    sim = L.from_case(case, progressive=progressive)
+    sim = L.from_case(case, progressive=progressive, storage=storage)
     sim.step(warmup)
     stream = torch.cuda.current_stream()
     st0 = sim.stats()
@@ -172,14 +175,14 @@ def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid):
     return out
 
 
-def run_e2e(L, torch, case, steps):
+def run_e2e(L, torch, case, steps, storage="fp32"):
     """End to end through the public API with host buffers: geometry and
     initial state uploaded, `steps` steps, both components' fields read
     back; wall clock around all of it."""
     import numpy as np
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = L.from_case(case)
+    sim = L.from_case(case, storage=storage)
     sim.step(steps)
     outs = [sim.macro(a) for a in range(2)]
     torch.cuda.synchronize()
@@ -272,6 +275,8 @@ def main():
                     help="grid edge (profiling captures use a smaller grid; the metric is 256)")
     ap.add_argument("--static-only", action="store_true",
                     help="time the static mesh only (profiling captures)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="population storage form (arithmetic is FP32 in all)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -292,7 +297,7 @@ def main():
     case = make_case(args.S, args.size)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if args.static_only:
-        st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid)
+        st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage)
         if rank == 0:
             print(json.dumps({"static_mlups": st["cells"] / (st["ms"] * 1e-3) / 1e6,
                               "ms": st["ms"], "kernel_ms": st["kernel_ms"],
@@ -302,7 +307,7 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid)
+    prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, args.storage)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -310,9 +315,9 @@ def main():
 
     stat = None
     if not args.no_static:
-        stat = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid)
+        stat = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage)
         s_max, s_cells = reduce_max_sum(dist, torch, stat["ms"], stat["cells"])
-    e2e = None if args.no_e2e else run_e2e(L, torch, case, args.warmup + args.steps)
+    e2e = None if args.no_e2e else run_e2e(L, torch, case, args.warmup + args.steps, args.storage)
     if e2e is not None:
         e_max, e_cells = reduce_max_sum(dist, torch, e2e["wall"], e2e["cells"])
 
@@ -322,14 +327,15 @@ def main():
         return 0
 
     peak, peak_kind = peaks()
+    bpu = BYTES_PER_UPDATE[args.storage]
     mlups = cells_sum / (t_max * 1e-3) / 1e6
     # algorithmic bytes: 304 B for every fluid cell updated (solid cells move
     # no data, held cells are read by their neighbours but never written)
-    step_frac = prog["fluid"] * BYTES_PER_UPDATE / (prog["ms"] * 1e-3) / 1e9 / peak
+    step_frac = prog["fluid"] * bpu / (prog["ms"] * 1e-3) / 1e9 / peak
     # dominant kernel: force + collide (kind 2)
     kms, kn = prog["kernel_ms"][2], prog["kernel_launches"][2]
-    coll_gbs = prog["fluid"] * BYTES_PER_UPDATE / (kms * 1e-3) / 1e9 if kms > 0 else None
-    traffic_pc = kernel_traffic()
+    coll_gbs = prog["fluid"] * bpu / (kms * 1e-3) / 1e9 if kms > 0 else None
+    traffic_pc = kernel_traffic(args.storage)
     avg_cells = prog["cells"] / max(kn, 1)
     avg_fluid = prog["fluid"] / max(kn, 1)
     roofline = {
@@ -339,7 +345,7 @@ def main():
         "traffic": round(traffic_pc * avg_cells) if traffic_pc else None,
         "kernel": "k_collide (force gather + exact-difference collision + pull streaming)",
         "peak_kind": peak_kind,
-        "algorithmic_bytes_per_launch": round(avg_fluid * BYTES_PER_UPDATE),
+        "algorithmic_bytes_per_launch": round(avg_fluid * bpu),
         "avg_launch_ms": round(kms / max(kn, 1), 5),
     }
     share = {name: round(v / max(sum(prog["kernel_ms"]), 1e-9), 4)
@@ -347,6 +353,7 @@ def main():
     config = {
         "workload": WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}",
         "mode": "progressive", "grid": [args.size] * 3, "block": [8, 8, 8],
+        "storage": args.storage,
         "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
         "mean_active_fraction": round(prog["cells"] / 512 / args.steps / prog["total_blocks"], 4),
@@ -359,7 +366,7 @@ def main():
         s_mlups = s_cells / (s_max * 1e-3) / 1e6
         config["static_mlups"] = round(s_mlups, 1)
         config["static_step_hbm_frac"] = round(
-            stat["fluid"] * BYTES_PER_UPDATE / (stat["ms"] * 1e-3) / 1e9 / peak, 4)
+            stat["fluid"] * bpu / (stat["ms"] * 1e-3) / 1e9 / peak, 4)
         config["progressive_over_static_time"] = round(prog["ms"] / stat["ms"], 4)
     cpu = None
     if not args.no_cpu:

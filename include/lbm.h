@@ -55,6 +55,17 @@ extern "C" {
 #define LBM_CELL_SOLID 1
 #define LBM_CELL_HELD 2
 
+/* Storage form of the populations (lbm_params.storage).  Arithmetic is FP32
+ * in every form.  The 16-bit forms store each population as its deviation
+ * f_i - w_i rho_r from the resting equilibrium of rho_r, the density that
+ * the cell which will read the value (the cell x + e_i, or x itself behind a
+ * solid wall) had at the step the value was written; a reader adds w_i
+ * times its own previous density back.  This is not part of the paper; it
+ * halves the population traffic of Eqs. 1 and 10. */
+#define LBM_STORAGE_FP32 0
+#define LBM_STORAGE_FP16 1 /* IEEE binary16 deviations */
+#define LBM_STORAGE_BF16 2 /* bfloat16 deviations */
+
 #define LBM_BLOCK_EDGE 8 /* cells per block edge */
 #define LBM_Q 19         /* D3Q19 populations per component */
 
@@ -72,6 +83,7 @@ typedef struct lbm_params {
     int periodic[3];     /* per axis: 1 wraps around, 0 ends in solid cells */
     int progressive;     /* 1: progressive mesh (Sec. 4); 0: static mesh, every
                             block holding a non-solid cell meshed from the start */
+    int storage;         /* LBM_STORAGE_FP32 (0), _FP16 or _BF16 */
     double tau;          /* BGK relaxation time, Eq. 1 (> 0.5) */
     double beta;         /* weighting term of Eq. 8 (the paper uses 1.16) */
     double pr_a, pr_b, pr_R, pr_omega; /* Peng-Robinson a, b, R, acentric factor, Eq. 7 */
@@ -109,9 +121,10 @@ typedef struct lbm_stats {
 } lbm_stats;
 
 /* Validate `p`, allocate the block pool (capacity x 2 buffers x ncomp x 19 x
- * 512 floats) and the tables, and return a new context in *out.  Allocates
- * through p->dev_alloc when given.  Errors: LBM_EINVAL (bad parameter: grid
- * not a multiple of 8, ncomp not 1 or 2, tau <= 0.5, S < 0, ...; no CUDA
+ * 512 populations of 4 bytes, or 2 in the 16-bit storage forms) and the
+ * tables, and return a new context in *out.  Allocates through p->dev_alloc
+ * when given.  Errors: LBM_EINVAL (bad parameter: grid not a multiple of 8,
+ * ncomp not 1 or 2, tau <= 0.5, S < 0, unknown storage form, ...; no CUDA
  * call is made then), LBM_ENOMEM, LBM_ECUDA.  On error *out is NULL. */
 int lbm_create(const lbm_params *p, lbm_ctx **out);
 
@@ -173,8 +186,9 @@ int lbm_mass(lbm_ctx *ctx, double *mass);
 
 /* Post-collision populations of one meshed block, host array
  * [ncomp][19][512] in the library's velocity order (lbm_velocities), cell
- * index x + 8 * (y + 8 * z) within the block.  LBM_EINVAL if the block is
- * not meshed. */
+ * index x + 8 * (y + 8 * z) within the block; in the 16-bit storage forms
+ * the stored deviations with their reference added back, in FP32, and 0 at
+ * solid cells.  LBM_EINVAL if the block is not meshed. */
 int lbm_get_block_populations(lbm_ctx *ctx, int32_t block_id, float *out);
 
 /* The library's D3Q19 velocity order: e[3 * i + axis], 19 x 3 ints. */

@@ -155,6 +155,9 @@ int validate(const lbm_params *p)
     if (!(p->S >= 0.0) || !std::isfinite(p->S))
         return fail(nullptr, LBM_EINVAL, "S must be >= 0, got %g", p->S);
     if (p->max_blocks < 0) return fail(nullptr, LBM_EINVAL, "max_blocks must be >= 0");
+    if (p->storage != LBM_STORAGE_FP32 && p->storage != LBM_STORAGE_FP16 &&
+        p->storage != LBM_STORAGE_BF16)
+        return fail(nullptr, LBM_EINVAL, "unknown storage form %d", p->storage);
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
         return fail(nullptr, LBM_EINVAL, "dev_alloc and dev_free must be given together");
     for (int a = 0; a < 3; ++a)
@@ -179,6 +182,7 @@ void fill_physics(lbm_ctx *c)
     k.ncomp = p.ncomp;
     k.capacity = c->capacity;
     k.progressive = p.progressive ? 1 : 0;
+    k.storage = p.storage;
     k.omega = (float)(1.0 / p.tau);
     k.beta = (float)p.beta;
     k.g_self = (float)p.g_self;
@@ -344,10 +348,11 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
         return bail(LBM_ECUDA);
     }
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
-    c->ctas_per_sm = max_ctas_per_sm_stream_kernels();
+    c->ctas_per_sm = max_ctas_per_sm_stream_kernels(p->storage);
     fill_physics(c);
 
-    const size_t slot_floats = (size_t)p->ncomp * Q * CELLS;
+    const bool dev16 = p->storage != LBM_STORAGE_FP32;
+    const size_t slot_floats = (size_t)(dev16 ? 1 : p->ncomp) * Q * CELLS;
     KParams &k = c->kp;
     k.slot_floats = (int)slot_floats;
     k.amb_slot = c->capacity;
@@ -360,11 +365,12 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
         void **dst;
         size_t bytes;
     } want[] = {
-        {(void **)&k.f, 2 * k.buf_stride * sizeof(float)},
-        {(void **)&k.mac, (size_t)(c->capacity + 1) * CELLS * sizeof(float4)},
+        {(void **)&k.f, dev16 ? 0 : 2 * k.buf_stride * sizeof(float)},
+        {(void **)&k.h, dev16 ? 2 * k.buf_stride * sizeof(uint32_t) : 0},
+        {(void **)&k.mac, (dev16 ? 2 : 1) * (size_t)(c->capacity + 1) * CELLS * sizeof(float4)},
         {(void **)&k.nbits, (size_t)c->capacity * CELLS * sizeof(uint32_t)},
         {(void **)&k.nbr, (size_t)c->capacity * NBR_STRIDE * sizeof(int)},
-        {(void **)&k.uprev, p->progressive ? (size_t)c->capacity * p->ncomp * 3 * CELLS * sizeof(float) : 0},
+        {(void **)&k.uprev, p->progressive || dev16 ? (size_t)c->capacity * p->ncomp * 3 * CELLS * sizeof(float) : 0},
         {(void **)&k.slot_of, (size_t)c->nblocks * sizeof(int)},
         {(void **)&k.block_of, (size_t)c->capacity * sizeof(int)},
         {(void **)&k.solid, (size_t)c->nblocks * MASK_WORDS * sizeof(uint32_t)},
@@ -386,9 +392,11 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
             return bail(LBM_ENOMEM);
         }
     }
-    // staging: up to 2048 blocks of [ncomp][4][CELLS] floats at a time
+    k.mac_stride = dev16 ? (size_t)(c->capacity + 1) * CELLS : 0;
+    // staging: up to 2048 blocks of [ncomp][4][CELLS] floats at a time, and
+    // at least one block's populations
     c->stage_floats = (size_t)std::min(c->capacity, 2048) * p->ncomp * 4 * CELLS;
-    if (c->stage_floats < 4 * CELLS) c->stage_floats = 4 * CELLS;
+    c->stage_floats = std::max(c->stage_floats, (size_t)p->ncomp * Q * CELLS);
     c->stage = (float *)dev_alloc(c, c->stage_floats * sizeof(float));
     if (!c->stage) {
         fail(c, LBM_ENOMEM, "staging allocation failed");
@@ -519,6 +527,8 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     Ctrl ctrl{};
     ctrl.n_active[0] = ctrl.n_active[1] = n0;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(k.ctrl, &ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
+    if (k.mac_stride)
+        CUDA_OR_FAIL(c, cudaMemsetAsync(k.mac, 0, 2 * k.mac_stride * sizeof(float4), s));
     CUDA_OR_FAIL(c, launch_ambient_slot(k, s));
     float psi_amb = 0.f;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(&psi_amb, &k.ctrl->psi_amb, sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -551,6 +561,9 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
         c->launches += 1;
         CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
     }
+    CUDA_OR_FAIL(c, launch_init_finish(k, n0, c->sms, s));
+    c->launches += k.mac_stride && n0 ? 1 : 0;
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
     c->slot_of_h = slot_of;
     c->step = 0;
     c->sticky = LBM_OK;
@@ -700,8 +713,15 @@ int lbm_get_block_populations(lbm_ctx *c, int32_t block_id, float *out)
     CUDA_OR_FAIL(c, cudaMemcpyAsync(&slot, c->kp.slot_of + block_id, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     if (slot < 0) return fail(c, LBM_EINVAL, "block %d is not meshed", block_id);
-    const float *src = c->kp.f + (size_t)(c->step & 1) * c->kp.buf_stride + (size_t)slot * c->kp.slot_floats;
-    CUDA_OR_FAIL(c, cudaMemcpyAsync(out, src, (size_t)c->kp.slot_floats * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    const int rd = (int)(c->step & 1);
+    const float *src = c->kp.f ? c->kp.f + (size_t)rd * c->kp.buf_stride + (size_t)slot * c->kp.slot_floats
+                               : c->stage;
+    if (!c->kp.f) {
+        CUDA_OR_FAIL(c, launch_block_pops(c->kp, rd, slot, c->stage, c->stream));
+        c->launches += 1;
+    }
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(out, src, (size_t)c->p.ncomp * Q * CELLS * sizeof(float),
+                                    cudaMemcpyDeviceToHost, c->stream));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }

@@ -45,6 +45,7 @@ struct KParams {
     int amb_slot;       // == capacity: a slot holding the resting ambient state
                         // (populations in both buffers, first-pass values)
     int progressive;
+    int storage;        // LBM_STORAGE_*
     // physics, FP32
     float omega;        // 1 / tau
     float beta, g_self, g_cross;
@@ -58,11 +59,19 @@ struct KParams {
     float psi_amb;
     float famb[2][Q];   // ambient resting populations w_i rho_amb
     // device memory
-    float *f;           // [2][capacity + 1][ncomp][Q][CELLS]
-    float4 *mac;        // [capacity + 1][CELLS]: rho0, psi0, rho1, 0 of the current step
+    float *f;           // FP32 form: [2][capacity + 1][ncomp][Q][CELLS]
+    uint32_t *h;        // 16-bit forms: [2][capacity + 1][Q][CELLS] words of
+                        // two 16-bit deviations from w_i rho of the reading
+                        // cell (component 0 low, component 1 high)
+    float4 *mac;        // [capacity + 1][CELLS]: rho0, psi0, rho1, 0 of the
+                        // current step; the 16-bit forms keep two of them,
+                        // by step parity (mac_stride apart), because the
+                        // previous step's densities are the references
+    size_t mac_stride;  // 0 (FP32 form) or (capacity + 1) * CELLS
     uint32_t *nbits;    // [capacity][CELLS]: bit i set when cell x - e_i is solid
                         // (bit 0: the cell itself), bit HELD_BIT: held cell
-    float *uprev;       // [capacity][ncomp][3][CELLS]
+    float *uprev;       // [capacity][ncomp][3][CELLS]; in the 16-bit forms
+                        // also the velocity of held cells
     int *slot_of;       // [nblocks]
     int *nbr;           // [capacity][NBR_STRIDE]: slots of the 27 blocks around a slot
     int *block_of;      // [capacity]
@@ -71,17 +80,39 @@ struct KParams {
     int *cand_list;     // [nblocks]
     unsigned *cand_mark;    // [nblocks]
     Ctrl *ctrl;
-    size_t buf_stride;  // floats per population buffer
-    int slot_floats;    // ncomp * Q * CELLS
+    size_t buf_stride;  // elements (floats or words) per population buffer
+    int slot_floats;    // elements per slot: ncomp * Q * CELLS (FP32) or
+                        // Q * CELLS (16-bit forms)
 };
 
 // Kernel kinds for per-kernel timing.
 enum KernelKind { K_MACRO = 0, K_ACTIVATE = 1, K_COLLIDE = 2, K_OTHER = 3 };
 
-// Launch wrappers (lbm_kernels.cu).  All enqueue on `s` and return the
-// launch status.
+// The kernels of one storage form (lbm_step.cuh, compiled once per form).
+struct StorageOps {
+    cudaError_t (*init)(const KParams &, const float *, int, int, int, cudaStream_t);
+    cudaError_t (*init_finish)(const KParams &, int, int, cudaStream_t);
+    cudaError_t (*ambient_slot)(const KParams &, cudaStream_t);
+    cudaError_t (*macro)(const KParams &, int, int, int, cudaStream_t);
+    cudaError_t (*activate)(const KParams &, int, int, cudaStream_t);
+    cudaError_t (*collide)(const KParams &, int, int, cudaStream_t);
+    cudaError_t (*output)(const KParams &, int, int, int, int, float *, int, cudaStream_t);
+    cudaError_t (*mass_partial)(const KParams &, int, int, double *, int, cudaStream_t);
+    cudaError_t (*block_pops)(const KParams &, int, int, float *, cudaStream_t);
+    int (*ctas_per_sm)();
+};
+const StorageOps *storage_ops_fp32();
+const StorageOps *storage_ops_fp16();
+const StorageOps *storage_ops_bf16();
+
+// Launch wrappers (lbm_kernels.cu), dispatching on kp.storage.  All enqueue
+// on `s` and return the launch status.
+// Initial state of slots [slot0, slot0 + nslots) from in_block; once every
+// initial slot is done, launch_init_finish (the 16-bit forms write their
+// populations there, when all reference densities are known).
 cudaError_t launch_init(const KParams &kp, const float *in_block, int slot0, int nslots,
                         int grid, cudaStream_t s);
+cudaError_t launch_init_finish(const KParams &kp, int nslots, int sms, cudaStream_t s);
 cudaError_t launch_ambient_slot(const KParams &kp, cudaStream_t s);
 // The cell kernels size their persistent grids themselves: `sms` x the
 // CTAs per SM their occupancy allows.
@@ -92,7 +123,9 @@ cudaError_t launch_output(const KParams &kp, int rd, int comp, int slot0, int ns
                           int sms, cudaStream_t s);
 cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, double *out, int grid,
                         cudaStream_t s);
-int max_ctas_per_sm_stream_kernels();
+// FP32 populations of one slot of buffer rd into out[ncomp][Q][CELLS] (16-bit forms).
+cudaError_t launch_block_pops(const KParams &kp, int rd, int slot, float *out, cudaStream_t s);
+int max_ctas_per_sm_stream_kernels(int storage);
 
 // Message returned by lbm_last_error(NULL) (lbm_capi.cpp).
 void set_global_error(const char *msg);

@@ -1,0 +1,1484 @@
+// Device side of liblbm: the progressive-mesh two-component pseudo-potential
+// LBM step (arXiv:1510.03560, Sec. 2 and Sec. 4) for sm_103a, written once
+// for every storage form of the populations and compiled once per form
+// (lbm_kernels.cu: FP32, lbm_kernels_f16.cu: FP16, lbm_kernels_bf16.cu:
+// BF16).
+//
+// Layout in HBM (block-major structure of arrays, Sec. 3: SoA for
+// coalescing):
+//   f[buf][slot][comp][dir][cell]   populations, two buffers (A-B pattern,
+//                                   Sec. 3), cell = x + 8 (y + 8 z); FP32,
+//                                   or 16-bit deviations (below)
+//   mac[par][slot][cell]            float4 (rho0, psi0, rho1, 0) of the step;
+//                                   one copy (FP32) or two by step parity
+//   nbits[slot][cell]               bit i: cell x - e_i is solid; bit 19: held
+//   uprev[slot][comp][3][cell]      velocity of the previous step, read and
+//                                   written only at cells bordering
+//                                   unmeshed blocks (criterion, Eq. 13)
+// A warp covers four x-rows of one z-plane of a block: every population
+// access of a warp touches consecutive sectors of one plane.
+//
+// 16-bit forms: the value stored at (x, i) is f_i - w_i rho_r, rho_r the
+// density at the writing step of the cell that reads it next (x + e_i, or x
+// itself when x + e_i is solid).  The writer (the collision) has gathered
+// those densities for the forces already; a reader needs only its own
+// previous density, one load per cell.  Populations coming from the
+// ambient state (unmeshed blocks, blocks created in this step) are the
+// ambient equilibrium itself.  Held cells keep their density in mac and
+// their velocity in uprev and are rewritten every step.
+//
+// The step kernels have no block-wide barrier.  A CTA of 256 threads works on
+// half a block at a time (grid-stride over half-blocks); every warp fetches
+// the slots of the 27 blocks around its block with one lane-parallel load
+// and hands them out with shuffles, and reads the per-cell solid bits
+// instead of block masks.
+//
+// One time step is three launches:
+//   k_macro    pull streaming + Eqs. 4-5 + Eqs. 6-7 -> mac; criterion of
+//              Eq. 13 at cells bordering unmeshed blocks, marking targets
+//   k_activate new blocks: slots, ambient equilibrium, their k_macro work
+//   k_collide  pull streaming again + forces (Eqs. 8-9, gravity,
+//              adhesion) from the neighbours' mac + forced BGK collision
+//              (Eqs. 10-12) -> f of the other buffer
+#pragma once
+
+#include <climits>
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+
+namespace lbm {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Checked builds (-DLBM_CHECKED) test the slot and block indices of the step
+// kernels before use; a failure records the site and value in the control
+// words (lbm_step then fails) and the access is skipped.  Normal builds
+// compile the checks away.
+#ifdef LBM_CHECKED
+__device__ __forceinline__ bool in_range(const KParams &kp, long long v, long long hi, int site)
+{
+    if (v >= 0 && v < hi) return true;
+    if (atomicCAS(&kp.ctrl->check_site, 0, site) == 0) kp.ctrl->check_value = v;
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_range(const KParams &, long long, long long, int) { return true; }
+#endif
+constexpr int THREADS = 256;            // threads per CTA of the cell kernels
+constexpr int DEV_MIN_CTAS = 3;         // resident CTAs per SM the deviation-form
+                                        // step kernels are compiled for
+constexpr int PARTS = CELLS / THREADS;  // CTA work items per block
+
+// ---- D3Q19 in this library's order: the 9 velocities with e_z = 0, then
+// the 5 with e_z = +1, then the 5 with e_z = -1; opposites are adjacent
+// within the first group and 5 apart across the other two. -------------
+__host__ __device__ constexpr int cx(int i)
+{
+    return (i == 1 || i == 5 || i == 7 || i == 10 || i == 16) ? 1
+           : (i == 2 || i == 6 || i == 8 || i == 11 || i == 15) ? -1
+                                                                 : 0;
+}
+__host__ __device__ constexpr int cy(int i)
+{
+    return (i == 3 || i == 5 || i == 8 || i == 12 || i == 18) ? 1
+           : (i == 4 || i == 6 || i == 7 || i == 13 || i == 17) ? -1
+                                                                 : 0;
+}
+__host__ __device__ constexpr int cz(int i) { return (i >= 9 && i <= 13) ? 1 : (i >= 14 ? -1 : 0); }
+__host__ __device__ constexpr int opp(int i)
+{
+    return i == 0 ? 0 : (i <= 8 ? ((i & 1) ? i + 1 : i - 1) : (i <= 13 ? i + 5 : i - 5));
+}
+__host__ __device__ constexpr float wgt(int i)
+{
+    return i == 0 ? 1.0f / 3.0f
+                  : ((i <= 4 || i == 9 || i == 14) ? 1.0f / 18.0f : 1.0f / 36.0f);
+}
+// One representative of each opposite pair, and the representative of any
+// moving velocity's pair.
+__host__ __device__ constexpr int pair_rep(int p)
+{
+    return p < 4 ? 1 + 2 * p : 5 + p;  // 1 3 5 7 | 9 10 11 12 13
+}
+__host__ __device__ constexpr int rep_of(int i)
+{
+    return i <= 8 ? ((i & 1) ? i : i - 1) : (i <= 13 ? i : i - 5);
+}
+constexpr int NPAIR = 9;
+
+template <int I, int N>
+struct Unroll {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&f)
+    {
+        f.template operator()<I>();
+        Unroll<I + 1, N>::run(f);
+    }
+};
+template <int N>
+struct Unroll<N, N> {
+    template <class F>
+    __device__ __forceinline__ static void run(F &&) {}
+};
+
+// ---- storage forms ----------------------------------------------------------
+// FP32: one float per (component, direction, cell).  Deviation forms: one
+// 32-bit word per (direction, cell) holding both components' 16-bit
+// deviations (component 0 in the low half), so that a warp's access moves
+// 128 bytes like the FP32 form's.
+template <int ST>
+struct Store;
+template <>
+struct Store<LBM_STORAGE_FP32> {
+    using T = float;
+    static constexpr bool DEV = false;
+};
+template <>
+struct Store<LBM_STORAGE_FP16> {
+    using T = uint32_t;
+    static constexpr bool DEV = true;
+    __device__ static __forceinline__ float2 dec2(uint32_t w)
+    {
+        return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(w & 0xffffu)),
+                                             __ushort_as_half((unsigned short)(w >> 16))));
+    }
+    __device__ static __forceinline__ uint32_t enc2(float a, float b)
+    {
+        const __half2 h = __floats2half2_rn(a, b);
+        return (uint32_t)__half_as_ushort(__low2half(h)) |
+               ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
+    }
+};
+template <>
+struct Store<LBM_STORAGE_BF16> {
+    using T = uint32_t;
+    static constexpr bool DEV = true;
+    __device__ static __forceinline__ float2 dec2(uint32_t w)
+    {
+        return make_float2(__bfloat162float(__ushort_as_bfloat16((unsigned short)(w & 0xffffu))),
+                           __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> 16))));
+    }
+    __device__ static __forceinline__ uint32_t enc2(float a, float b)
+    {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return (uint32_t)__bfloat16_as_ushort(__low2bfloat16(h)) |
+               ((uint32_t)__bfloat16_as_ushort(__high2bfloat16(h)) << 16);
+    }
+};
+
+template <int ST>
+__device__ __forceinline__ typename Store<ST>::T *pops(const KParams &kp)
+{
+    if constexpr (ST == LBM_STORAGE_FP32)
+        return kp.f;
+    else
+        return reinterpret_cast<uint32_t *>(kp.h);
+}
+
+// Neighbour-block index (0..26) of a local coordinate in [-1, 8].
+__device__ __forceinline__ int side(int v) { return v < 0 ? 0 : (v > 7 ? 2 : 1); }
+__device__ __forceinline__ int nbk(int x, int y, int z) { return side(x) + 3 * side(y) + 9 * side(z); }
+__device__ __forceinline__ int lcell(int x, int y, int z)
+{
+    return (x & 7) | ((y & 7) << 3) | ((z & 7) << 6);
+}
+
+__device__ __forceinline__ int neighbour_block(const KParams &kp, int x, int y, int z)
+{
+    if (x < 0 || x >= kp.nbx) {
+        if (!kp.per[0]) return -1;
+        x = (x + kp.nbx) % kp.nbx;
+    }
+    if (y < 0 || y >= kp.nby) {
+        if (!kp.per[1]) return -1;
+        y = (y + kp.nby) % kp.nby;
+    }
+    if (z < 0 || z >= kp.nbz) {
+        if (!kp.per[2]) return -1;
+        z = (z + kp.nbz) % kp.nbz;
+    }
+    return x + kp.nbx * (y + kp.nby * z);
+}
+
+__device__ __forceinline__ int neighbour_of(const KParams &kp, int gid, int k)
+{
+    const int bx = gid % kp.nbx, by = (gid / kp.nbx) % kp.nby, bz = gid / (kp.nbx * kp.nby);
+    return neighbour_block(kp, bx + k % 3 - 1, by + (k / 3) % 3 - 1, bz + k / 9 - 1);
+}
+
+// The 27 blocks around `gid`, one slot per lane (lane 13: the block itself,
+// or unmeshed with own_unmeshed; lanes 27-31: SOLIDBLK), and the
+// warp-uniform mask of unmeshed neighbours.  Slots >= slot_limit count as
+// unmeshed.  Every lane of the warp calls it.
+struct WarpNbr {
+    int slot;         // slot, AMBIENT or SOLIDBLK
+    unsigned amb;     // warp-uniform: bit k set when neighbour k is unmeshed
+    uint32_t fbase;   // population offset of the slot (the ambient slot for
+                      // unmeshed or solid blocks)
+    uint32_t mbase;   // first-pass value offset in kp.mac, likewise (plus
+                      // the offset of the parity in use)
+};
+
+__device__ __forceinline__ WarpNbr make_nbr(const KParams &kp, int s, uint32_t moff = 0)
+{
+    const uint32_t q = s >= 0 ? (uint32_t)s : (uint32_t)kp.amb_slot;
+    return WarpNbr{s, __ballot_sync(FULL, s == AMBIENT) & ~(1u << 13), q * (uint32_t)kp.slot_floats,
+                   q * (uint32_t)CELLS + moff};
+}
+
+__device__ __forceinline__ WarpNbr warp_nbr(const KParams &kp, int gid, int own_slot, int slot_limit,
+                                            bool own_unmeshed = false)
+{
+    const int lane = threadIdx.x & 31;
+    int s = SOLIDBLK;
+    if (lane == 13) {
+        s = own_unmeshed ? AMBIENT : own_slot;
+    } else if (lane < 27) {
+        const int nid = neighbour_of(kp, gid, lane);
+        if (nid >= 0) {
+            s = kp.slot_of[nid];
+            if (s >= slot_limit) s = AMBIENT;
+        }
+    }
+    return make_nbr(kp, s);
+}
+
+// The same, read from the slot's row of the neighbour-slot table (kept up to
+// date by block creation): one coalesced 128-byte load per warp.
+__device__ __forceinline__ int nbr_row_lane(const KParams &kp, int slot)
+{
+    return kp.nbr[(size_t)slot * NBR_STRIDE + (threadIdx.x & 31)];
+}
+__device__ __forceinline__ WarpNbr warp_nbr_of(const KParams &kp, int lane_slot, uint32_t moff = 0)
+{
+    return make_nbr(kp, lane_slot, moff);
+}
+
+
+
+// Neighbour blocks reachable from a cell through the 18 moving velocities.
+__device__ __forceinline__ unsigned reach_bits(int lx, int ly, int lz)
+{
+    unsigned r = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) r |= 1u << nbk(lx + cx(i), ly + cy(i), lz + cz(i));
+    return r & ~(1u << 13);
+}
+
+// Solid / held word of one cell from the per-block masks (bit i: x - e_i is
+// solid, cells outside a non-periodic axis are solid; bit HELD_BIT: held).
+__device__ uint32_t cell_bits(const KParams &kp, int gid, int c)
+{
+    const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int sx = lx - cx(i), sy = ly - cy(i), sz = lz - cz(i);
+        const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+        const int nid = k == 13 ? gid : neighbour_of(kp, gid, k);
+        const bool solid =
+            nid < 0 || ((kp.solid[(size_t)nid * MASK_WORDS + (lc >> 5)] >> (lc & 31)) & 1u);
+        bits |= (uint32_t)solid << i;
+    }
+    if ((kp.held[(size_t)gid * MASK_WORDS + (c >> 5)] >> (c & 31)) & 1u) bits |= 1u << HELD_BIT;
+    return bits;
+}
+
+// Source offset (in the read buffer) of the population moving along e_I
+// into cell c: from x - e_I; the cell's own opposite population behind a
+// solid cell (halfway bounce-back); its own population at held cells.
+// `own` is the cell's own offset.  Every lane calls (one shuffle).
+template <int I>
+__device__ __forceinline__ uint32_t src_offset(const WarpNbr &wn, uint32_t own, int lx, int ly,
+                                               int lz, uint32_t bits, bool held, int &k)
+{
+    const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+    k = nbk(sx, sy, sz);
+    const int lc = lcell(sx, sy, sz);
+    const uint32_t base = __shfl_sync(FULL, wn.fbase, k);
+    const bool bounce = (bits >> I) & 1u;
+    return held ? own + (uint32_t)(I * CELLS)
+                : (bounce ? own + (uint32_t)(opp(I) * CELLS) : base + (uint32_t)(I * CELLS + lc));
+}
+
+// The loads of one cell's pull in a deviation form, issued but not yet
+// used: one packed word per direction, and which populations come from
+// the ambient state (unmeshed source blocks, or the cell's own block when
+// it was created in this step).
+struct DevLoad {
+    uint32_t v[Q];
+    uint32_t ambs;
+};
+
+template <int ST>
+__device__ __forceinline__ void dev_issue(const KParams &kp, const WarpNbr &wn, const uint32_t *rd,
+                                          int own_slot, int c, uint32_t bits, bool live,
+                                          bool own_ambient, DevLoad &L)
+{
+    const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+    const uint32_t own =
+        (own_ambient ? (uint32_t)kp.amb_slot : (uint32_t)own_slot) * (uint32_t)kp.slot_floats + (uint32_t)c;
+    const bool held = (bits >> HELD_BIT) & 1u;
+    const unsigned ambm = wn.amb | (own_ambient ? (1u << 13) : 0u);
+    uint32_t off[Q];
+    uint32_t ambs = 0;
+    Unroll<0, Q>::run([&]<int I>() {
+        int k;
+        off[I] = src_offset<I>(wn, own, lx, ly, lz, bits, held, k);
+        const bool bounce = (bits >> I) & 1u;
+        const bool a = (held || bounce) ? own_ambient : ((ambm >> k) & 1u);
+        ambs |= (uint32_t)a << I;
+    });
+    L.ambs = ambs;
+    Unroll<0, Q>::run([&]<int I>() { L.v[I] = live ? __ldg(rd + off[I]) : 0u; });
+}
+
+// Decode the loads of dev_issue: the FP32 populations are the stored
+// deviations plus w_I rho_prev (the cell's own previous density `ref`), or
+// plus the ambient equilibrium for ambient sources; sink(a, I, f) in pull
+// order.
+template <int NC, int ST, class Sink>
+__device__ __forceinline__ void dev_consume(const KParams &kp, const DevLoad &L, const float ref[2],
+                                            Sink &&sink)
+{
+    auto one = [&]<int I>() {
+        const float2 x = Store<ST>::dec2(L.v[I]);
+        const bool amb = (L.ambs >> I) & 1u;
+        sink.template operator()<I>(0, amb ? kp.famb[0][I] + x.x : __fmaf_rn(wgt(I), ref[0], x.x));
+        if constexpr (NC == 2)
+            sink.template operator()<I>(1, amb ? kp.famb[1][I] + x.y : __fmaf_rn(wgt(I), ref[1], x.y));
+    };
+    one.template operator()<0>();
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        one.template operator()<pair_rep(P)>();
+        one.template operator()<opp(pair_rep(P))>();
+    });
+}
+
+// Pull streaming (Eq. 10, left-hand side) of every component of one cell,
+// rest first, then opposite pairs, handing each arriving population to
+// sink(a, I, v).  The population moving along e_I comes from x - e_I:
+// halfway bounce-back when that cell is solid, the ambient resting
+// population when its block is unmeshed, the stored value otherwise; held
+// cells keep their own.  With own_ambient the cell's own block is one created
+// in this step, still at the ambient state, and is not read back.  In the
+// deviation forms `ref` is the cell's own density of the previous step
+// (the reference its incoming values were written against) and held cells'
+// values are not meaningful.  All lanes must call (shuffles); `live` masks
+// the loads.
+template <int NC, int ST, class Sink>
+__device__ __forceinline__ void pull(const KParams &kp, const WarpNbr &wn,
+                                     const typename Store<ST>::T *rd, int own_slot, int c, int lx,
+                                     int ly, int lz, uint32_t bits, bool live, bool own_ambient,
+                                     const float ref[2], Sink &&sink)
+{
+    if constexpr (Store<ST>::DEV) {
+        DevLoad L;
+        dev_issue<ST>(kp, wn, rd, own_slot, c, bits, live, own_ambient, L);
+        dev_consume<NC, ST>(kp, L, ref, sink);
+    } else {
+        const uint32_t own = (own_ambient ? (uint32_t)kp.amb_slot : (uint32_t)own_slot) *
+                                 (uint32_t)kp.slot_floats + (uint32_t)c;
+        const bool held = (bits >> HELD_BIT) & 1u;
+        // Three phases, so that all of a cell's loads are in flight together:
+        // (1) the source offset of every population (32-bit, from the read
+        // buffer; one shuffle each: unmeshed blocks read the ambient slot),
+        // (2) every load, (3) the sink.
+        uint32_t off[Q];
+        Unroll<0, Q>::run([&]<int I>() {
+            const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+            const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+            const uint32_t base = __shfl_sync(FULL, wn.fbase, k);
+            const bool bounce = (bits >> I) & 1u;
+            off[I] = held ? own + (uint32_t)(I * CELLS)
+                          : (bounce ? own + (uint32_t)(opp(I) * CELLS) : base + (uint32_t)(I * CELLS + lc));
+        });
+        float v[NC][Q];
+        Unroll<0, Q>::run([&]<int I>() {
+#pragma unroll
+            for (int c2 = 0; c2 < NC; ++c2) v[c2][I] = live ? __ldg(rd + off[I] + c2 * Q * CELLS) : 0.f;
+        });
+        auto one = [&]<int I>() {
+#pragma unroll
+            for (int c2 = 0; c2 < NC; ++c2) sink.template operator()<I>(c2, v[c2][I]);
+        };
+        one.template operator()<0>();
+        Unroll<0, NPAIR>::run([&]<int P>() {
+            one.template operator()<pair_rep(P)>();
+            one.template operator()<opp(pair_rep(P))>();
+        });
+    }
+}
+
+// Deviation forms: the reference density of each population a cell writes,
+// the previous-step density of the cell that reads it (rd[a][i]; the cell
+// itself for the rest population and behind solid cells), from `mac`.
+// Unmeshed readers give the ambient values (the ambient slot).  All lanes
+// must call; `gather` masks the loads.
+template <int NC>
+__device__ __forceinline__ void reader_refs(const WarpNbr &wn, const float4 *mac, int lx, int ly,
+                                            int lz, uint32_t bits, bool gather, const float own[2],
+                                            float rdst[2][Q])
+{
+#pragma unroll
+    for (int a = 0; a < NC; ++a) rdst[a][0] = own[a];
+    Unroll<1, Q>::run([&]<int D>() {
+        const int tx = lx + cx(D), ty = ly + cy(D), tz = lz + cz(D);
+        const int k = nbk(tx, ty, tz), lc = lcell(tx, ty, tz);
+        const uint32_t mb = __shfl_sync(FULL, wn.mbase, k);
+        const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
+        const float4 m = gather ? __ldg(mac + mb + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
+        rdst[0][D] = solid_n ? own[0] : m.x;
+        if (NC == 2) rdst[1][D] = solid_n ? own[1] : m.z;
+    });
+}
+
+// Eqs. 4-5 accumulated in pull order: the density as a running sum, the
+// momentum from each opposite pair's difference.
+struct Moments {
+    float rho[2] = {0.f, 0.f};
+    float j[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    float first[2] = {0.f, 0.f};
+    template <int I>
+    __device__ __forceinline__ void add(int a, float v)
+    {
+        rho[a] += v;
+        if constexpr (I == 0) {
+            return;
+        } else if constexpr (rep_of(I) == I) {
+            first[a] = v;
+        } else {
+            constexpr int R = rep_of(I);
+            const float d = first[a] - v;
+            if (cx(R) > 0) j[a][0] += d; else if (cx(R) < 0) j[a][0] -= d;
+            if (cy(R) > 0) j[a][1] += d; else if (cy(R) < 0) j[a][1] -= d;
+            if (cz(R) > 0) j[a][2] += d; else if (cz(R) < 0) j[a][2] -= d;
+        }
+    }
+};
+
+// Eq. 7 (Peng-Robinson) and Eq. 6 (pseudo-potential), FP32.
+__device__ __forceinline__ float psi_of(const KParams &kp, float rho)
+{
+    if (kp.g_self == 0.f) return 0.f;
+    const float b = kp.pr_b;
+    const float p = rho * kp.pr_RT / (1.f - b * rho) -
+                    kp.pr_atheta * rho * rho / (1.f + 2.f * b * rho - b * b * rho * rho);
+    const float arg = kp.psi_scale * (p - rho * (1.0f / 3.0f));
+    return sqrtf(fmaxf(arg, 0.f));
+}
+
+// Eq. 2 with c_s^2 = 1/3.
+template <int I>
+__device__ __forceinline__ float feq(float wrho, float ux, float uy, float uz, float uu)
+{
+    float eu = 0.f;
+    if (cx(I) > 0) eu += ux; else if (cx(I) < 0) eu -= ux;
+    if (cy(I) > 0) eu += uy; else if (cy(I) < 0) eu -= uy;
+    if (cz(I) > 0) eu += uz; else if (cz(I) < 0) eu -= uz;
+    return wrho * (1.f + 3.f * eu + 4.5f * eu * eu - 1.5f * uu);
+}
+
+// ---------------------------------------------------------------------------
+// Initial state: equilibrium of the initial fields in both buffers, the
+// initial velocity as the "previous" one, the cells' solid words.  The
+// deviation forms write the densities (mac of parity 1, the reference of
+// step 0's reads) and velocities here and the populations in k_init_dev,
+// once every initial block's density is known.
+// in: [slot - slot0][ncomp][4][CELLS] (rho, ux, uy, uz), block-major.
+template <int ST>
+__global__ void __launch_bounds__(CELLS) k_init(KParams kp, const float *in, int slot0, int nslots)
+{
+    using S = Store<ST>;
+    const int c = threadIdx.x;
+    for (int r = blockIdx.x; r < nslots; r += gridDim.x) {
+        const int slot = slot0 + r;
+        const int gid = kp.block_of[slot];
+        const uint32_t bits = cell_bits(kp, gid, c);
+        kp.nbits[(size_t)slot * CELLS + c] = bits;
+        const bool solid = bits & 1u;
+        const unsigned fluid = __ballot_sync(FULL, !solid && !((bits >> HELD_BIT) & 1u));
+        if ((c & 31) == 0 && fluid)
+            atomicAdd(&kp.ctrl->fluid_active, (unsigned long long)__popc(fluid));
+        float rho_c[2] = {0.f, 0.f};
+        for (int a = 0; a < kp.ncomp; ++a) {
+            const float *src = in + ((size_t)r * kp.ncomp + a) * 4 * CELLS;
+            float rho = src[c], ux = src[CELLS + c], uy = src[2 * CELLS + c],
+                  uz = src[3 * CELLS + c];
+            if (solid) rho = ux = uy = uz = 0.f;
+            rho_c[a] = rho;
+            if constexpr (!S::DEV) {
+                const float uu = ux * ux + uy * uy + uz * uz;
+                float *d0 = kp.f + (size_t)slot * kp.slot_floats + a * Q * CELLS + c;
+                float *d1 = d0 + kp.buf_stride;
+                Unroll<0, Q>::run([&]<int I>() {
+                    const float v = feq<I>(wgt(I) * rho, ux, uy, uz, uu);
+                    d0[I * CELLS] = v;
+                    d1[I * CELLS] = v;
+                });
+            }
+            if (kp.uprev) {
+                float *up = kp.uprev + ((size_t)slot * kp.ncomp + a) * 3 * CELLS + c;
+                up[0] = ux;
+                up[CELLS] = uy;
+                up[2 * CELLS] = uz;
+            }
+        }
+        if constexpr (S::DEV)
+            kp.mac[kp.mac_stride + (size_t)slot * CELLS + c] =
+                solid ? make_float4(0.f, 0.f, 0.f, 0.f)
+                      : make_float4(rho_c[0], psi_of(kp, rho_c[0]), rho_c[1], 0.f);
+    }
+}
+
+// Deviation forms: the populations of buffer 0 for the initial slots, the
+// equilibrium of (mac[1], uprev) written against the reading cells'
+// densities, the rest population from the mass balance.
+template <int NC, int ST>
+__global__ void __launch_bounds__(THREADS) k_init_dev(KParams kp, int nslots)
+{
+    using S = Store<ST>;
+    const float4 *ref = kp.mac + kp.mac_stride;
+    typename S::T *d_all = pops<ST>(kp);
+    for (int it = blockIdx.x; it < nslots * PARTS; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
+        const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+        const bool live = !(bits & 1u);
+        const float4 m = __ldg(ref + (size_t)slot * CELLS + c);
+        const float own[2] = {m.x, m.z};
+        float rdst[2][Q];
+        reader_refs<NC>(wn, ref, lx, ly, lz, bits, live, own, rdst);
+        uint32_t *dst = d_all + (size_t)slot * kp.slot_floats + c;
+        if (!live) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) dst[i * CELLS] = 0u;
+            continue;
+        }
+        float ux[2], uy[2], uz[2], uu[2], moving[2] = {0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+            ux[a] = up[0];
+            uy[a] = up[CELLS];
+            uz[a] = up[2 * CELLS];
+            uu[a] = ux[a] * ux[a] + uy[a] * uy[a] + uz[a] * uz[a];
+        }
+        Unroll<1, Q>::run([&]<int I>() {
+            float d[2] = {0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < NC; ++a)
+                d[a] = __fmaf_rn(-wgt(I), rdst[a][I], feq<I>(wgt(I) * own[a], ux[a], uy[a], uz[a], uu[a]));
+            const uint32_t h = S::enc2(d[0], d[1]);
+            dst[I * CELLS] = h;
+            const float2 back = S::dec2(h);
+            moving[0] += __fmaf_rn(wgt(I), rdst[0][I], back.x);
+            moving[1] += __fmaf_rn(wgt(I), rdst[1][I], back.y);
+        });
+        dst[0] = S::enc2(__fmaf_rn(-wgt(0), own[0], own[0] - moving[0]),
+                         NC == 2 ? __fmaf_rn(-wgt(0), own[1], own[1] - moving[1]) : 0.f);
+    }
+}
+
+// The ambient slot: resting ambient populations in both buffers (zero
+// deviations in the 16-bit forms) and the ambient first-pass values, read
+// wherever a neighbour block is unmeshed.
+template <int ST>
+__global__ void __launch_bounds__(CELLS) k_ambient_slot(KParams kp)
+{
+    using S = Store<ST>;
+    const int c = threadIdx.x;
+    const float psi = psi_of(kp, kp.rho_amb[0]);
+    if (c == 0) kp.ctrl->psi_amb = psi;
+    typename S::T *base = pops<ST>(kp) + (size_t)kp.amb_slot * kp.slot_floats + c;
+    for (int i = 0; i < kp.slot_floats / CELLS; ++i) {
+        typename S::T v{};
+        if constexpr (!S::DEV) v = kp.famb[i / Q][i % Q];
+        base[i * CELLS] = v;
+        base[kp.buf_stride + i * CELLS] = v;
+    }
+    const float4 m = make_float4(kp.rho_amb[0], psi, kp.rho_amb[1], 0.f);
+    kp.mac[(size_t)kp.amb_slot * CELLS + c] = m;
+    kp.mac[kp.mac_stride + (size_t)kp.amb_slot * CELLS + c] = m;
+}
+
+// Streaming + moments of one cell; writes mac (live cells), returns rho and
+// the bare velocity.  In the deviation forms `ref` is the cell's previous
+// density and a held cell's mac stays `prev`.  All lanes must call.
+template <int NC, int ST>
+__device__ __forceinline__ void macro_cell(const KParams &kp, const WarpNbr &wn,
+                                           const typename Store<ST>::T *rd, float4 *mac, int slot,
+                                           int c, int lx, int ly, int lz, uint32_t bits, bool live,
+                                           bool own_ambient, const float ref[2], float4 prev,
+                                           float rho[2], float u[2][3])
+{
+    Moments m;
+    pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, own_ambient, ref,
+                 [&]<int I>(int a, float v) { m.template add<I>(a, v); });
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        rho[a] = m.rho[a];
+        const float inv = 1.f / m.rho[a];
+        u[a][0] = m.j[a][0] * inv;
+        u[a][1] = m.j[a][1] * inv;
+        u[a][2] = m.j[a][2] * inv;
+    }
+    if (live) {
+        float4 out = make_float4(rho[0], psi_of(kp, rho[0]), NC == 2 ? rho[1] : 0.f, 0.f);
+        if constexpr (Store<ST>::DEV)
+            if ((bits >> HELD_BIT) & 1u) out = prev;
+        mac[(size_t)slot * CELLS + c] = out;
+    }
+}
+
+// Eq. 13 at a fluid cell bordering unmeshed blocks: when the velocity of a
+// component changed by more than S since the previous step, the unmeshed
+// blocks next to the cell become candidates.  Warp-collective.
+template <int NC>
+__device__ __forceinline__ void criterion_mark(const KParams &kp, Ctrl *ctrl, int par, int n, int slot,
+                                               int c, const WarpNbr &wn, bool fluid,
+                                               const float u[2][3])
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned front = reach_bits(c & 7, (c >> 3) & 7, c >> 6) & wn.amb;
+    unsigned tgt = 0;
+    if (fluid && front) {
+        float d2max = 0.f;
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+            const float dx = u[a][0] - up[0], dy = u[a][1] - up[CELLS], dz = u[a][2] - up[2 * CELLS];
+            d2max = fmaxf(d2max, dx * dx + dy * dy + dz * dz);
+        }
+        if (d2max > kp.S2) tgt = front;
+    }
+    tgt = __reduce_or_sync(FULL, tgt);
+    if (tgt && lane < 27 && ((tgt >> lane) & 1u)) {
+        // a candidate takes the next slot after the meshed ones now
+        // (k_activate checks the capacity and undoes it if full)
+        const int nid = neighbour_of(kp, kp.block_of[slot], lane);
+        if (in_range(kp, nid, (long long)kp.nbx * kp.nby * kp.nbz, 3) &&
+            atomicCAS(&kp.cand_mark[nid], 0u, 1u) == 0u) {
+            const int pos = atomicAdd(&ctrl->ncand[par], 1);
+            kp.cand_list[pos] = nid;
+            if (n + pos < kp.capacity) kp.slot_of[nid] = n + pos;
+        }
+    }
+}
+
+// Pass 1 of a step (FP32 form): streaming and moments over the meshed
+// blocks; with `criterion`, Eq. 13 at fluid cells bordering unmeshed blocks.
+template <int NC>
+__global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int criterion)
+{
+    constexpr int ST = LBM_STORAGE_FP32;
+    Ctrl *ctrl = kp.ctrl;
+    if (criterion && ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;
+    const int total = n * PARTS;
+    // the neighbour row and solid word of the next item are fetched while
+    // the current one is processed
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+        }
+        const bool live = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        // (warp-uniform: the pull below shuffles)
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
+        float rho[2], u[2][3];
+        const float ref[2] = {0.f, 0.f};
+        macro_cell<NC, ST>(kp, wn, rd, kp.mac, slot, c, lx, ly, lz, bits, live, false, ref,
+                           make_float4(0.f, 0.f, 0.f, 0.f), rho, u);
+        if (criterion) criterion_mark<NC>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
+    }
+}
+
+// Work items of the deviation-form kernels, software-pipelined: the next
+// item's population loads are issued before the current item is processed,
+// so that they are in flight during its arithmetic.
+struct DevItem {
+    int slot, c;
+    bool ok;          // warp-uniform: the item's table entries passed the checks
+    uint32_t bits;
+    WarpNbr wn;
+    DevLoad L;
+    float ref[2];     // the cell's previous density (mac of the other parity)
+};
+
+template <int ST>
+__device__ __forceinline__ void dev_item(const KParams &kp, const uint32_t *rd, const float4 *mac_prev,
+                                         int it, int row, uint32_t bits, uint32_t moff, DevItem &d)
+{
+    d.slot = it / PARTS;
+    d.c = (it % PARTS) * THREADS + threadIdx.x;
+    d.bits = bits;
+    d.wn = warp_nbr_of(kp, row, moff);
+    d.ok = __all_sync(FULL, in_range(kp, d.wn.slot + 2, (long long)kp.capacity + 2, 2));
+    const bool nonsolid = !(bits & 1u);
+    const bool held = (bits >> HELD_BIT) & 1u;
+    dev_issue<ST>(kp, d.wn, rd, d.slot, d.c, bits, d.ok && nonsolid && !held, false, d.L);
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (d.ok && nonsolid) p = __ldg(mac_prev + (size_t)d.slot * CELLS + d.c);
+    d.ref[0] = p.x;
+    d.ref[1] = p.z;
+}
+
+// Pass 1 of a step in the deviation forms (as k_macro).  Held cells keep
+// their density: mac of this step is a copy of the previous one.
+template <int NC, int ST>
+__global__ void __launch_bounds__(THREADS, DEV_MIN_CTAS) k_macro_dev(KParams kp, int step, int criterion)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (criterion && ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
+    const uint32_t *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
+    float4 *mac = kp.mac + (size_t)par * kp.mac_stride;
+    const float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
+    const int total = n * PARTS;
+    const int G = gridDim.x;
+    int it = blockIdx.x;
+    if (it >= total) return;
+    DevItem cur;
+    dev_item<ST>(kp, rd, mac_prev, it, nbr_row_lane(kp, it / PARTS),
+                 kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x], 0u, cur);
+    int it2 = it + G;
+    int row2 = it2 < total ? nbr_row_lane(kp, it2 / PARTS) : SOLIDBLK;
+    uint32_t bits2 =
+        it2 < total ? kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += G) {
+        DevItem nxt;
+        if (it2 < total) {
+            dev_item<ST>(kp, rd, mac_prev, it2, row2, bits2, 0u, nxt);
+            const int it3 = it2 + G;
+            if (it3 < total) {
+                row2 = nbr_row_lane(kp, it3 / PARTS);
+                bits2 = kp.nbits[(size_t)(it3 / PARTS) * CELLS + (it3 % PARTS) * THREADS + threadIdx.x];
+            }
+        }
+        if (cur.ok) {
+            const bool live = !(cur.bits & 1u);
+            const bool held = (cur.bits >> HELD_BIT) & 1u;
+            Moments m;
+            dev_consume<NC, ST>(kp, cur.L, cur.ref, [&]<int I>(int a, float v) { m.template add<I>(a, v); });
+            float u[2][3];
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const float inv = 1.f / m.rho[a];
+                u[a][0] = m.j[a][0] * inv;
+                u[a][1] = m.j[a][1] * inv;
+                u[a][2] = m.j[a][2] * inv;
+            }
+            if (live)
+                mac[(size_t)cur.slot * CELLS + cur.c] =
+                    held ? make_float4(cur.ref[0], psi_of(kp, cur.ref[0]), cur.ref[1], 0.f)
+                         : make_float4(m.rho[0], psi_of(kp, m.rho[0]), NC == 2 ? m.rho[1] : 0.f, 0.f);
+            if (criterion) criterion_mark<NC>(kp, ctrl, par, n, cur.slot, cur.c, cur.wn, live && !held, u);
+        }
+        cur = nxt;
+        it2 += G;
+    }
+}
+
+// Block creation (Sec. 4.2-4.3): the candidates found by k_macro get slots
+// after the meshed ones, start from the ambient resting equilibrium in both
+// buffers (R14) and get their streaming and moments of this step computed,
+// with every block created in this step seen as ambient.  The deviation
+// forms write the read buffer only (the collision of this step writes every
+// non-solid cell of the other one), against the previous densities of the
+// reading cells, and give the block the ambient density as its previous one.
+template <int NC, int ST>
+__global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
+{
+    using S = Store<ST>;
+    Ctrl *ctrl = kp.ctrl;
+    if (ctrl->status) return;
+    const int par = step & 1;
+    const int n_old = ctrl->n_active[par];
+    const int ncand = ctrl->ncand[par];
+    if (!in_range(kp, ncand, (long long)kp.nbx * kp.nby * kp.nbz + 1, 4)) return;
+    if (n_old + ncand > kp.capacity) {
+        // the pool cannot hold them: undo the slots k_macro handed out, so
+        // the state stays that of the last completed step
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncand; k += gridDim.x * blockDim.x) {
+            const int gid = kp.cand_list[k];
+            kp.slot_of[gid] = AMBIENT;
+            kp.cand_mark[gid] = 0u;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctrl->status = LBM_ENOMEM;
+            ctrl->fail_step = step;
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->n_active[par ^ 1] = n_old + ncand;
+        ctrl->ncand[par ^ 1] = 0;
+    }
+    typename S::T *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
+    float4 *mac = kp.mac + (size_t)par * kp.mac_stride;
+    float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
+    for (int it = blockIdx.x; it < ncand * PARTS; it += gridDim.x) {
+        const int k = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int slot = n_old + k;
+        const int gid = kp.cand_list[k];
+        if (!in_range(kp, gid, (long long)kp.nbx * kp.nby * kp.nbz, 5)) continue;
+        if (c == 0) kp.block_of[slot] = gid;
+        if (c < 32) {
+            // the new block's row of the neighbour-slot table, and its slot in
+            // the rows of its meshed neighbours (every candidate's slot is
+            // already set, so the two writers of an entry agree)
+            int s = SOLIDBLK;
+            if (c == 13) {
+                s = slot;
+            } else if (c < 27) {
+                const int nid = neighbour_of(kp, gid, c);
+                if (nid >= 0) s = kp.slot_of[nid];
+                if (s >= 0 && in_range(kp, s, kp.capacity, 6))
+                    kp.nbr[(size_t)s * NBR_STRIDE + (26 - c)] = slot;
+            }
+            kp.nbr[(size_t)slot * NBR_STRIDE + c] = s;
+        }
+        const uint32_t bits = cell_bits(kp, gid, c);
+        kp.nbits[(size_t)slot * CELLS + c] = bits;
+        const bool live = !(bits & 1u);
+        const unsigned fluid = __ballot_sync(FULL, live && !((bits >> HELD_BIT) & 1u));
+        if ((threadIdx.x & 31) == 0 && fluid)
+            atomicAdd(&ctrl->fluid_active, (unsigned long long)__popc(fluid));
+        const WarpNbr wn = warp_nbr(kp, gid, slot, n_old, true);
+        const float4 amb = make_float4(kp.rho_amb[0], kp.psi_amb, kp.rho_amb[1], 0.f);
+        if constexpr (!S::DEV) {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                float *d0 = kp.f + (size_t)slot * kp.slot_floats + a * Q * CELLS + c;
+                float *d1 = d0 + kp.buf_stride;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    d0[i * CELLS] = kp.famb[a][i];
+                    d1[i * CELLS] = kp.famb[a][i];
+                }
+            }
+        } else {
+            // blocks created in this step (slots >= n_old) are ambient
+            // readers, like the unmeshed ones
+            float rdst[2][Q];
+            reader_refs<NC>(wn, mac_prev, lx, ly, lz, bits, live, kp.rho_amb, rdst);
+            uint32_t *d = rd + (size_t)slot * kp.slot_floats + c;
+            Unroll<0, Q>::run([&]<int I>() {
+                d[I * CELLS] = live ? S::enc2(__fmaf_rn(-wgt(I), rdst[0][I], kp.famb[0][I]),
+                                              NC == 2 ? __fmaf_rn(-wgt(I), rdst[1][I], kp.famb[1][I]) : 0.f)
+                                    : 0u;
+            });
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+                up[0] = up[CELLS] = up[2 * CELLS] = 0.f;
+            }
+            mac_prev[(size_t)slot * CELLS + c] = live ? amb : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float rho[2], u[2][3];
+        macro_cell<NC, ST>(kp, wn, rd, mac, slot, c, lx, ly, lz, bits, live, true, kp.rho_amb, amb, rho, u);
+    }
+}
+
+// Forces on a fluid cell (Eqs. 8-9 as read, gravity, adhesion), from the
+// mac values of its 18 neighbours.  A solid neighbour lends the centre's own
+// values; an unmeshed one the ambient values.  The mac copy in use starts
+// at kp.mac + moff (wn.mbase includes moff; addressing from the kernel
+// parameter keeps the gather's address registers down).  With REFS the
+// neighbours' densities are also returned per direction (rdst, the reading
+// cells' references of the deviation forms).  All lanes must call; `live`
+// masks the loads.
+template <int NC, bool REFS = false>
+__device__ __forceinline__ void forces(const KParams &kp, const WarpNbr &wn, uint32_t moff,
+                                       int slot, int c, int lx, int ly, int lz, uint32_t bits,
+                                       bool live, const float rho[2], float F[2][3],
+                                       float rdst[2][Q] = nullptr)
+{
+    const float psi_c = live ? kp.mac[(size_t)moff + (size_t)slot * CELLS + c].y : 0.f;
+    const float r0c = rho[0], r1c = NC == 2 ? rho[1] : 0.f;
+    float sp[3] = {0, 0, 0}, sp2[3] = {0, 0, 0}, sr0[3] = {0, 0, 0}, sr1[3] = {0, 0, 0},
+          ss[3] = {0, 0, 0};
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        constexpr int I = pair_rep(P);
+        constexpr int J = opp(I);
+        float psi_n[2], r0_n[2], r1_n[2], s_n[2];
+        Unroll<0, 2>::run([&]<int H>() {
+            constexpr int D = H == 0 ? I : J;
+            const int tx = lx + cx(D), ty = ly + cy(D), tz = lz + cz(D);
+            const int k = nbk(tx, ty, tz), lc = lcell(tx, ty, tz);
+            const uint32_t mb = __shfl_sync(FULL, wn.mbase, k);
+            const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
+            const float4 m = live ? __ldg(kp.mac + mb + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
+            psi_n[H] = solid_n ? psi_c : m.y;
+            r0_n[H] = solid_n ? r0c : m.x;
+            r1_n[H] = solid_n ? r1c : m.z;
+            s_n[H] = solid_n ? 1.f : 0.f;
+            if constexpr (REFS) {
+                rdst[0][D] = r0_n[H];
+                if (NC == 2) rdst[1][D] = r1_n[H];
+            }
+        });
+        const float w = wgt(I);
+        const float dp = w * (psi_n[0] - psi_n[1]);
+        const float dp2 = w * (psi_n[0] * psi_n[0] - psi_n[1] * psi_n[1]);
+        const float d0 = w * (r0_n[0] - r0_n[1]);
+        const float d1 = w * (r1_n[0] - r1_n[1]);
+        const float ds = w * (s_n[0] - s_n[1]);
+        const int e[3] = {cx(I), cy(I), cz(I)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (e[d] > 0) {
+                sp[d] += dp; sp2[d] += dp2; sr0[d] += d0; sr1[d] += d1; ss[d] += ds;
+            } else if (e[d] < 0) {
+                sp[d] -= dp; sp2[d] -= dp2; sr0[d] -= d0; sr1[d] -= d1; ss[d] -= ds;
+            }
+        }
+    });
+    const float a1 = -kp.beta * kp.g_self * psi_c;
+    const float a2 = -(1.f - kp.beta) * 0.5f * kp.g_self;
+    const float ex0 = fmaxf(r0c - kp.rho_amb[0], 0.f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float f0 = a1 * sp[d] + a2 * sp2[d] - kp.g_ads[0] * ex0 * ss[d] +
+                   (r0c - kp.rho_ref[0]) * kp.grav[d];
+        if (NC == 2) f0 -= kp.g_cross * r0c * sr1[d];
+        F[0][d] = f0;
+    }
+    if (NC == 2) {
+        const float ex1 = fmaxf(r1c - kp.rho_amb[1], 0.f);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            F[1][d] = -kp.g_cross * r1c * sr0[d] - kp.g_ads[1] * ex1 * ss[d] +
+                      (r1c - kp.rho_ref[1]) * kp.grav[d];
+    }
+}
+
+// Pass 2 of a step (FP32 form): streaming again, forces, forced BGK
+// collision (Eqs. 10-12, R1 sign), store into the other buffer; the
+// velocity is kept for the next criterion at cells that border unmeshed
+// blocks.
+template <int NC, bool TAU1>
+__global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
+{
+    constexpr int ST = LBM_STORAGE_FP32;
+    Ctrl *ctrl = kp.ctrl;
+    if (ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par ^ 1];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 7)) return;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;
+    float *wr = kp.f + (size_t)(par ^ 1) * kp.buf_stride;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->cell_updates += (unsigned long long)n * CELLS;
+        ctrl->fluid_updates += ctrl->fluid_active;
+    }
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+        }
+        const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) continue;
+        Moments m;
+        float fin[TAU1 ? 1 : NC][Q];
+        const float ref[2] = {0.f, 0.f};
+        pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, ref,
+                     [&]<int I>(int a, float v) {
+                         m.template add<I>(a, v);
+                         if constexpr (!TAU1) fin[a][I] = v;
+                     });
+        float rho[2] = {m.rho[0], m.rho[1]}, u[2][3];
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const float inv = 1.f / rho[a];
+            u[a][0] = m.j[a][0] * inv;
+            u[a][1] = m.j[a][1] * inv;
+            u[a][2] = m.j[a][2] * inv;
+        }
+        float F[2][3];
+        forces<NC>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
+        if (!live) continue;
+#pragma unroll
+        for (int a = 0; a < NC; ++a) {
+            const float inv = 1.f / rho[a];
+            const float vx = u[a][0] + F[a][0] * inv, vy = u[a][1] + F[a][1] * inv,
+                        vz = u[a][2] + F[a][2] * inv;
+            const float vv = vx * vx + vy * vy + vz * vz;
+            const float uu = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
+            float *dst = wr + (size_t)slot * kp.slot_floats + a * Q * CELLS + c;
+            const float r = rho[a];
+            // The 18 moving populations from Eqs. 10-12; the rest population
+            // from the mass balance sum_i f_i = rho, which the collision
+            // satisfies exactly in real arithmetic.  In FP32 this keeps the
+            // mass free of the systematic bias of the rounded weights
+            // (fl(1/3) + 6 fl(1/18) + 12 fl(1/36) = 1 + 1.5e-8).
+            float moving = 0.f;
+            Unroll<1, Q>::run([&]<int I>() {
+                const float wr_ = wgt(I) * r;
+                float v = feq<I>(wr_, vx, vy, vz, vv);
+                if constexpr (!TAU1) {
+                    const float e0 = feq<I>(wr_, u[a][0], u[a][1], u[a][2], uu);
+                    v += (1.f - kp.omega) * (fin[a][I] - e0);
+                }
+                moving += v;
+                dst[I * CELLS] = v;
+            });
+            dst[0] = r - moving;
+        }
+        if (kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+                up[0] = u[a][0];
+                up[CELLS] = u[a][1];
+                up[2 * CELLS] = u[a][2];
+            }
+        }
+    }
+}
+
+// Pass 2 of a step in the deviation forms (as k_collide, software-pipelined
+// like k_macro_dev).  Every value is stored against the density its reader
+// has now: the neighbour's mac of this step, the cell's own behind a solid
+// cell and for the rest population.  Held cells write their constant
+// equilibrium (density from mac, velocity from uprev).
+template <int NC, bool TAU1, int ST>
+__global__ void __launch_bounds__(THREADS, DEV_MIN_CTAS) k_collide_dev(KParams kp, int step)
+{
+    using S = Store<ST>;
+    Ctrl *ctrl = kp.ctrl;
+    if (ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par ^ 1];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 7)) return;
+    const uint32_t *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
+    uint32_t *wr = pops<ST>(kp) + (size_t)(par ^ 1) * kp.buf_stride;
+    const uint32_t moff = (uint32_t)(par * kp.mac_stride);
+    const float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->cell_updates += (unsigned long long)n * CELLS;
+        ctrl->fluid_updates += ctrl->fluid_active;
+    }
+    const int total = n * PARTS;
+    const int G = gridDim.x;
+    int it = blockIdx.x;
+    if (it >= total) return;
+    DevItem cur;
+    dev_item<ST>(kp, rd, mac_prev, it, nbr_row_lane(kp, it / PARTS),
+                 kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x], moff, cur);
+    int it2 = it + G;
+    int row2 = it2 < total ? nbr_row_lane(kp, it2 / PARTS) : SOLIDBLK;
+    uint32_t bits2 =
+        it2 < total ? kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += G) {
+        DevItem nxt;
+        if (it2 < total) {
+            dev_item<ST>(kp, rd, mac_prev, it2, row2, bits2, moff, nxt);
+            const int it3 = it2 + G;
+            if (it3 < total) {
+                row2 = nbr_row_lane(kp, it3 / PARTS);
+                bits2 = kp.nbits[(size_t)(it3 / PARTS) * CELLS + (it3 % PARTS) * THREADS + threadIdx.x];
+            }
+        }
+        if (cur.ok) {
+            const int slot = cur.slot, c = cur.c;
+            const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+            const uint32_t bits = cur.bits;
+            const bool nonsolid = !(bits & 1u);
+            const bool held = (bits >> HELD_BIT) & 1u;
+            const bool live = nonsolid && !held;
+            Moments m;
+            float fin[TAU1 ? 1 : NC][Q];
+            dev_consume<NC, ST>(kp, cur.L, cur.ref, [&]<int I>(int a, float v) {
+                m.template add<I>(a, v);
+                if constexpr (!TAU1) fin[a][I] = v;
+            });
+            float rho[2] = {m.rho[0], m.rho[1]}, u[2][3];
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const float inv = 1.f / rho[a];
+                u[a][0] = m.j[a][0] * inv;
+                u[a][1] = m.j[a][1] * inv;
+                u[a][2] = m.j[a][2] * inv;
+                if (held) {
+                    const float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+                    rho[a] = cur.ref[a];
+                    u[a][0] = up[0];
+                    u[a][1] = up[CELLS];
+                    u[a][2] = up[2 * CELLS];
+                }
+            }
+            float F[2][3];
+            forces<NC>(kp, cur.wn, moff, slot, c, lx, ly, lz, bits, nonsolid, rho, F);
+            // every lane runs the collision (its shuffles need the whole
+            // warp); solid cells store nothing
+            float vx[2], vy[2], vz[2], vv[2], uu[2], moving[2] = {0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                const float inv = held ? 0.f : 1.f / rho[a];
+                vx[a] = u[a][0] + F[a][0] * inv;
+                vy[a] = u[a][1] + F[a][1] * inv;
+                vz[a] = u[a][2] + F[a][2] * inv;
+                vv[a] = vx[a] * vx[a] + vy[a] * vy[a] + vz[a] * vz[a];
+                uu[a] = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
+            }
+            uint32_t *dst = wr + (size_t)slot * kp.slot_floats + c;
+            // The 18 moving populations (Eqs. 10-12), each against its
+            // reader's density; the rest population from the mass balance
+            // over the values as their readers will decode them, so that it
+            // absorbs the rounding of the other 18.
+            Unroll<1, Q>::run([&]<int I>() {
+                const int tx = lx + cx(I), ty = ly + cy(I), tz = lz + cz(I);
+                const uint32_t mb = __shfl_sync(FULL, cur.wn.mbase, nbk(tx, ty, tz));
+                const bool solid_n = (bits >> opp(I)) & 1u;  // x + e_I = x - e_opp(I)
+                const float4 mr = (solid_n || !nonsolid) ? make_float4(rho[0], 0.f, rho[1], 0.f)
+                                                         : __ldg(kp.mac + mb + lcell(tx, ty, tz));
+                const float rr[2] = {mr.x, mr.z};
+                float d[2] = {0.f, 0.f};
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    const float wr_ = wgt(I) * rho[a];
+                    float v = feq<I>(wr_, vx[a], vy[a], vz[a], vv[a]);
+                    if constexpr (!TAU1) {
+                        if (!held) {
+                            const float e0 = feq<I>(wr_, u[a][0], u[a][1], u[a][2], uu[a]);
+                            v += (1.f - kp.omega) * (fin[a][I] - e0);
+                        }
+                    }
+                    d[a] = __fmaf_rn(-wgt(I), rr[a], v);
+                }
+                const uint32_t h = S::enc2(d[0], d[1]);
+                if (nonsolid) dst[I * CELLS] = h;
+                const float2 back = S::dec2(h);
+                moving[0] += __fmaf_rn(wgt(I), rr[0], back.x);
+                moving[1] += __fmaf_rn(wgt(I), rr[1], back.y);
+            });
+            if (nonsolid)
+                dst[0] = S::enc2(__fmaf_rn(-wgt(0), rho[0], rho[0] - moving[0]),
+                                 NC == 2 ? __fmaf_rn(-wgt(0), rho[1], rho[1] - moving[1]) : 0.f);
+            if (live && kp.progressive && (reach_bits(lx, ly, lz) & cur.wn.amb)) {
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+                    up[0] = u[a][0];
+                    up[CELLS] = u[a][1];
+                    up[2 * CELLS] = u[a][2];
+                }
+            }
+        }
+        cur = nxt;
+        it2 += G;
+    }
+}
+
+// Macroscopic output of one component for slots [slot0, slot0 + nslots):
+// out[slot - slot0][4][CELLS] = rho, ux, uy, uz, velocity u + F / (2 rho)
+// at fluid cells (R9), own moments at held cells, zeros at solid cells.
+// Expects mac of this step (k_macro without the criterion).
+template <int NC, int ST>
+__global__ void __launch_bounds__(THREADS) k_output(KParams kp, int rdbuf, int comp, int slot0,
+                                                    int nslots, float *out)
+{
+    using S = Store<ST>;
+    const typename S::T *rd = pops<ST>(kp) + (size_t)rdbuf * kp.buf_stride;
+    const uint32_t moff = S::DEV ? (uint32_t)(rdbuf * kp.mac_stride) : 0u;
+    const float4 *mac_prev = kp.mac + (size_t)(rdbuf ^ 1) * kp.mac_stride;
+    for (int it = blockIdx.x; it < nslots * PARTS; it += gridDim.x) {
+        const int r = it / PARTS;
+        const int slot = slot0 + r;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot), moff);
+        const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+        const bool live = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        float ref[2] = {0.f, 0.f};
+        if constexpr (S::DEV) {
+            if (live) {
+                const float4 p = __ldg(mac_prev + (size_t)slot * CELLS + c);
+                ref[0] = p.x;
+                ref[1] = p.z;
+            }
+        }
+        Moments m;
+        pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, ref,
+                     [&]<int I>(int a, float v) { m.template add<I>(a, v); });
+        float rho[2] = {m.rho[0], m.rho[1]};
+        float F[2][3];
+        forces<NC>(kp, wn, moff, slot, c, lx, ly, lz, bits, live && !held, rho, F);
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+        if (live) {
+            const int a = comp;
+            const float inv = 1.f / rho[a];
+            o[0] = rho[a];
+            o[1] = m.j[a][0] * inv;
+            o[2] = m.j[a][1] * inv;
+            o[3] = m.j[a][2] * inv;
+            if (!held) {
+                const float h = 0.5f * inv;
+                o[1] += F[a][0] * h;
+                o[2] += F[a][1] * h;
+                o[3] += F[a][2] * h;
+            } else if (S::DEV) {
+                const float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
+                o[0] = ref[a];
+                o[1] = up[0];
+                o[2] = up[CELLS];
+                o[3] = up[2 * CELLS];
+            }
+        }
+        float *dst = out + (size_t)r * 4 * CELLS + c;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q * CELLS] = o[q];
+    }
+}
+
+// The stored populations of one cell of buffer rdbuf as FP32 values (the
+// deviation forms add their readers' references back, from the mac of the
+// step that wrote them); zeros at solid cells.  All lanes of the warp call.
+template <int ST>
+__device__ __forceinline__ void stored_cell(const KParams &kp, int rdbuf, int slot, int c,
+                                            float out[2][Q])
+{
+    using S = Store<ST>;
+    const typename S::T *src = pops<ST>(kp) + (size_t)rdbuf * kp.buf_stride +
+                               (size_t)slot * kp.slot_floats + c;
+    const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+    const bool live = !(bits & 1u);
+    float rdst[2][Q];
+    if constexpr (S::DEV) {
+        const float4 *mref = kp.mac + (size_t)(rdbuf ^ 1) * kp.mac_stride;
+        const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
+        const float4 m = live ? __ldg(mref + (size_t)slot * CELLS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float own[2] = {m.x, m.z};
+        reader_refs<2>(wn, mref, c & 7, (c >> 3) & 7, c >> 6, bits, live, own, rdst);
+    }
+    if constexpr (S::DEV) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const float2 x = S::dec2(__ldg(src + i * CELLS));
+            out[0][i] = live ? __fmaf_rn(wgt(i), rdst[0][i], x.x) : 0.f;
+            out[1][i] = live ? __fmaf_rn(wgt(i), rdst[1][i], x.y) : 0.f;
+        }
+    } else {
+        for (int a = 0; a < kp.ncomp; ++a)
+#pragma unroll
+            for (int i = 0; i < Q; ++i) out[a][i] = __ldg(src + (a * Q + i) * CELLS);
+    }
+}
+
+// FP64 mass: per-slot partial sums over non-solid cells, then one CTA adds
+// the partials in a fixed order.
+template <int ST>
+__global__ void __launch_bounds__(CELLS) k_mass_partial(KParams kp, int rdbuf, int n,
+                                                        double *partial)
+{
+    __shared__ double red[CELLS / 32][2];
+    const int c = threadIdx.x;
+    for (int slot = blockIdx.x; slot < n; slot += gridDim.x) {
+        const bool solid = kp.nbits[(size_t)slot * CELLS + c] & 1u;
+        float f[2][Q];
+        stored_cell<ST>(kp, rdbuf, slot, c, f);
+        double m[2] = {0.0, 0.0};
+        for (int a = 0; a < kp.ncomp; ++a) {
+            if (solid) continue;
+            double acc = 0.0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) acc += (double)f[a][i];
+            m[a] = acc;
+        }
+        for (int a = 0; a < 2; ++a)
+            for (int o = 16; o > 0; o >>= 1) m[a] += __shfl_down_sync(FULL, m[a], o);
+        if ((c & 31) == 0) {
+            red[c >> 5][0] = m[0];
+            red[c >> 5][1] = m[1];
+        }
+        __syncthreads();
+        if (c < 2) {
+            double t = 0.0;
+            for (int w = 0; w < CELLS / 32; ++w) t += red[w][c];
+            partial[(size_t)slot * 2 + c] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// The populations of one slot, decoded to FP32: out[ncomp][Q][CELLS].
+template <int ST>
+__global__ void __launch_bounds__(CELLS) k_block_pops(KParams kp, int rdbuf, int slot, float *out)
+{
+    const int c = threadIdx.x;
+    float f[2][Q];
+    stored_cell<ST>(kp, rdbuf, slot, c, f);
+    for (int a = 0; a < kp.ncomp; ++a)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out[(a * Q + i) * CELLS + c] = f[a][i];
+}
+
+// ---- launch wrappers of one storage form -------------------------------------
+
+// Resident CTAs per SM of a kernel, looked up once per process.
+template <auto Kern>
+int occupancy()
+{
+    static int cached = 0;
+    if (!cached) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Kern, THREADS, 0) != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+        }
+        cached = n > 0 ? n : 1;
+    }
+    return cached;
+}
+
+template <auto Kern, class... A>
+cudaError_t launch_persistent(int sms, cudaStream_t s, A... args)
+{
+    Kern<<<sms * occupancy<Kern>(), THREADS, 0, s>>>(args...);
+    return cudaGetLastError();
+}
+
+template <int ST>
+struct Launch {
+    static cudaError_t init(const KParams &kp, const float *in_block, int slot0, int nslots, int grid,
+                            cudaStream_t s)
+    {
+        if (nslots <= 0) return cudaSuccess;
+        k_init<ST><<<grid, CELLS, 0, s>>>(kp, in_block, slot0, nslots);
+        return cudaGetLastError();
+    }
+    static cudaError_t init_finish(const KParams &kp, int nslots, int sms, cudaStream_t s)
+    {
+        if constexpr (!Store<ST>::DEV) {
+            return cudaSuccess;
+        } else {
+            if (nslots <= 0) return cudaSuccess;
+            if (kp.ncomp == 2) return launch_persistent<k_init_dev<2, ST>>(sms, s, kp, nslots);
+            return launch_persistent<k_init_dev<1, ST>>(sms, s, kp, nslots);
+        }
+    }
+    static cudaError_t ambient_slot(const KParams &kp, cudaStream_t s)
+    {
+        k_ambient_slot<ST><<<1, CELLS, 0, s>>>(kp);
+        return cudaGetLastError();
+    }
+    static cudaError_t macro(const KParams &kp, int step, int criterion, int sms, cudaStream_t s)
+    {
+        if constexpr (Store<ST>::DEV) {
+            if (kp.ncomp == 2) return launch_persistent<k_macro_dev<2, ST>>(sms, s, kp, step, criterion);
+            return launch_persistent<k_macro_dev<1, ST>>(sms, s, kp, step, criterion);
+        } else {
+            if (kp.ncomp == 2) return launch_persistent<k_macro<2>>(sms, s, kp, step, criterion);
+            return launch_persistent<k_macro<1>>(sms, s, kp, step, criterion);
+        }
+    }
+    static cudaError_t activate(const KParams &kp, int step, int sms, cudaStream_t s)
+    {
+        if (kp.ncomp == 2)
+            k_activate<2, ST><<<sms, THREADS, 0, s>>>(kp, step);
+        else
+            k_activate<1, ST><<<sms, THREADS, 0, s>>>(kp, step);
+        return cudaGetLastError();
+    }
+    static cudaError_t collide(const KParams &kp, int step, int sms, cudaStream_t s)
+    {
+        const bool tau1 = kp.omega == 1.0f;
+        if constexpr (Store<ST>::DEV) {
+            if (kp.ncomp == 2) {
+                if (tau1) return launch_persistent<k_collide_dev<2, true, ST>>(sms, s, kp, step);
+                return launch_persistent<k_collide_dev<2, false, ST>>(sms, s, kp, step);
+            }
+            if (tau1) return launch_persistent<k_collide_dev<1, true, ST>>(sms, s, kp, step);
+            return launch_persistent<k_collide_dev<1, false, ST>>(sms, s, kp, step);
+        } else {
+            if (kp.ncomp == 2) {
+                if (tau1) return launch_persistent<k_collide<2, true>>(sms, s, kp, step);
+                return launch_persistent<k_collide<2, false>>(sms, s, kp, step);
+            }
+            if (tau1) return launch_persistent<k_collide<1, true>>(sms, s, kp, step);
+            return launch_persistent<k_collide<1, false>>(sms, s, kp, step);
+        }
+    }
+    static cudaError_t output(const KParams &kp, int rd, int comp, int slot0, int nslots, float *out,
+                              int sms, cudaStream_t s)
+    {
+        if (nslots <= 0) return cudaSuccess;
+        if (kp.ncomp == 2)
+            return launch_persistent<k_output<2, ST>>(sms, s, kp, rd, comp, slot0, nslots, out);
+        return launch_persistent<k_output<1, ST>>(sms, s, kp, rd, comp, slot0, nslots, out);
+    }
+    static cudaError_t mass_partial(const KParams &kp, int rd, int n, double *partial, int grid,
+                                    cudaStream_t s)
+    {
+        if (n <= 0) return cudaSuccess;
+        k_mass_partial<ST><<<grid, CELLS, 0, s>>>(kp, rd, n, partial);
+        return cudaGetLastError();
+    }
+    static cudaError_t block_pops(const KParams &kp, int rd, int slot, float *out, cudaStream_t s)
+    {
+        k_block_pops<ST><<<1, CELLS, 0, s>>>(kp, rd, slot, out);
+        return cudaGetLastError();
+    }
+    // CTAs per SM that both streaming kernels can keep resident
+    static int ctas_per_sm()
+    {
+        int a, b;
+        if constexpr (Store<ST>::DEV) {
+            a = occupancy<k_collide_dev<2, true, ST>>();
+            b = occupancy<k_macro_dev<2, ST>>();
+        } else {
+            a = occupancy<k_collide<2, true>>();
+            b = occupancy<k_macro<2>>();
+        }
+        return a < b ? a : b;
+    }
+    static const StorageOps *ops()
+    {
+        static const StorageOps table = {init,   init_finish, ambient_slot, macro,      activate,
+                                         collide, output,     mass_partial, block_pops, ctas_per_sm};
+        return &table;
+    }
+};
+
+}  // namespace
+}  // namespace lbm

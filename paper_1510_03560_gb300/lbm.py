@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm_checked.so" if os.environ.get("LBM_CHECKED
                         else "liblbm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, 1, 2, 3, 4
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}  # LBM_STORAGE_*
 Q = 19
 EDGE = 8
 
@@ -31,6 +32,7 @@ class Params(C.Structure):
         ("ncomp", C.c_int),
         ("periodic", C.c_int * 3),
         ("progressive", C.c_int),
+        ("storage", C.c_int),
         ("tau", C.c_double), ("beta", C.c_double),
         ("pr_a", C.c_double), ("pr_b", C.c_double), ("pr_R", C.c_double), ("pr_omega", C.c_double),
         ("T_over_Tc", C.c_double),
@@ -158,8 +160,9 @@ class LBM:
     """One simulation context (lbm_ctx).
 
     Keyword parameters mirror lbm_params: nx, ny, nz, ncomp, periodic,
-    progressive, tau, beta, pr_a, pr_b, pr_R, pr_omega, T_over_Tc, g_self,
-    g_cross, g_ads, grav, rho_ref, S, max_blocks.  ``stream``: a
+    progressive, storage ("fp32", "fp16", "bf16" or the LBM_STORAGE_* code),
+    tau, beta, pr_a, pr_b, pr_R, pr_omega, T_over_Tc, g_self, g_cross, g_ads,
+    grav, rho_ref, S, max_blocks.  ``stream``: a
     torch.cuda.Stream (default: the current stream).  ``torch_alloc``:
     allocate through torch's caching allocator (default) or let the library
     use cudaMallocAsync.
@@ -181,6 +184,9 @@ class LBM:
         for a in range(3):
             p.periodic[a] = int(per[a])
         p.progressive = int(kw.get("progressive", 1))
+        st = kw.get("storage", 0)
+        p.storage = STORAGE[st] if isinstance(st, str) else int(st)
+        self.storage = p.storage
         p.tau = float(kw.get("tau", 1.0))
         p.beta = float(kw.get("beta", 1.16))
         p.pr_a = float(kw.get("pr_a", 2.0 / 49.0))

@@ -80,6 +80,8 @@ def _params(**over):
     (dict(tau=0.5), "tau"),
     (dict(S=-1.0), "S must be"),
     (dict(max_blocks=-2), "max_blocks"),
+    (dict(storage=3), "storage form"),
+    (dict(storage=-1), "storage form"),
 ])
 def test_create_rejects_bad_parameters_without_cuda(lib, over, frag):
     h = C.c_void_p()
