@@ -63,7 +63,7 @@ struct KParams {
     uint32_t *h;        // 16-bit forms: [2][capacity + 1][Q][CELLS] words of
                         // two 16-bit deviations from w_i rho of the reading
                         // cell (component 0 low, component 1 high)
-    float4 *mac;        // [capacity + 1][CELLS]: rho0, psi0, rho1, 0 of the
+    float4 *mac;        // [capacity + 1][CELLS]: rho0, rho1, psi0, 0 of the
                         // current step; the 16-bit forms keep two of them,
                         // by step parity (mac_stride apart), because the
                         // previous step's densities are the references

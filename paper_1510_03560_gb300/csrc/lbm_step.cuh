@@ -9,7 +9,7 @@
 //   f[buf][slot][comp][dir][cell]   populations, two buffers (A-B pattern,
 //                                   Sec. 3), cell = x + 8 (y + 8 z); FP32,
 //                                   or 16-bit deviations (below)
-//   mac[par][slot][cell]            float4 (rho0, psi0, rho1, 0) of the step;
+//   mac[par][slot][cell]            float4 (rho0, rho1, psi0, 0) of the step;
 //                                   one copy (FP32) or two by step parity
 //   nbits[slot][cell]               bit i: cell x - e_i is solid; bit 19: held
 //   uprev[slot][comp][3][cell]      velocity of the previous step, read and
@@ -71,8 +71,10 @@ __device__ __forceinline__ bool in_range(const KParams &kp, long long v, long lo
 __device__ __forceinline__ bool in_range(const KParams &, long long, long long, int) { return true; }
 #endif
 constexpr int THREADS = 256;            // threads per CTA of the cell kernels
-constexpr int DEV_MIN_CTAS = 3;         // resident CTAs per SM the deviation-form
-                                        // step kernels are compiled for
+// resident CTAs per SM the deviation-form step kernels are compiled for
+// (fewer registers would spill)
+constexpr int DEV_MACRO_MIN_CTAS = 3;
+constexpr int DEV_COLLIDE_MIN_CTAS = 2;
 constexpr int PARTS = CELLS / THREADS;  // CTA work items per block
 
 // ---- D3Q19 in this library's order: the 9 velocities with e_z = 0, then
@@ -145,30 +147,33 @@ struct Store<LBM_STORAGE_FP16> {
     static constexpr bool DEV = true;
     __device__ static __forceinline__ float2 dec2(uint32_t w)
     {
-        return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(w & 0xffffu)),
-                                             __ushort_as_half((unsigned short)(w >> 16))));
+        __half2 h;
+        __builtin_memcpy(&h, &w, 4);
+        return __half22float2(h);
     }
     __device__ static __forceinline__ uint32_t enc2(float a, float b)
     {
         const __half2 h = __floats2half2_rn(a, b);
-        return (uint32_t)__half_as_ushort(__low2half(h)) |
-               ((uint32_t)__half_as_ushort(__high2half(h)) << 16);
+        uint32_t w;
+        __builtin_memcpy(&w, &h, 4);
+        return w;
     }
 };
 template <>
 struct Store<LBM_STORAGE_BF16> {
     using T = uint32_t;
     static constexpr bool DEV = true;
+    // a bfloat16 is the upper half of the FP32 with the same value
     __device__ static __forceinline__ float2 dec2(uint32_t w)
     {
-        return make_float2(__bfloat162float(__ushort_as_bfloat16((unsigned short)(w & 0xffffu))),
-                           __bfloat162float(__ushort_as_bfloat16((unsigned short)(w >> 16))));
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
     }
     __device__ static __forceinline__ uint32_t enc2(float a, float b)
     {
         const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return (uint32_t)__bfloat16_as_ushort(__low2bfloat16(h)) |
-               ((uint32_t)__bfloat16_as_ushort(__high2bfloat16(h)) << 16);
+        uint32_t w;
+        __builtin_memcpy(&w, &h, 4);
+        return w;
     }
 };
 
@@ -416,6 +421,36 @@ __device__ __forceinline__ void pull(const KParams &kp, const WarpNbr &wn,
     }
 }
 
+// pull() of the FP32 form for two components, handing both components of
+// each direction to sink(I, (f_0, f_1)) together.
+template <class Sink>
+__device__ __forceinline__ void pull2_f32(const KParams &kp, const WarpNbr &wn, const float *rd,
+                                          int own_slot, int c, int lx, int ly, int lz, uint32_t bits,
+                                          bool live, Sink &&sink)
+{
+    const uint32_t own = (uint32_t)own_slot * (uint32_t)kp.slot_floats + (uint32_t)c;
+    const bool held = (bits >> HELD_BIT) & 1u;
+    uint32_t off[Q];
+    Unroll<0, Q>::run([&]<int I>() {
+        const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+        const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+        const uint32_t base = __shfl_sync(FULL, wn.fbase, k);
+        const bool bounce = (bits >> I) & 1u;
+        off[I] = held ? own + (uint32_t)(I * CELLS)
+                      : (bounce ? own + (uint32_t)(opp(I) * CELLS) : base + (uint32_t)(I * CELLS + lc));
+    });
+    float2 v[Q];
+    Unroll<0, Q>::run([&]<int I>() {
+        v[I] = live ? make_float2(__ldg(rd + off[I]), __ldg(rd + off[I] + Q * CELLS))
+                    : make_float2(0.f, 0.f);
+    });
+    sink.template operator()<0>(v[0]);
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        sink.template operator()<pair_rep(P)>(v[pair_rep(P)]);
+        sink.template operator()<opp(pair_rep(P))>(v[opp(pair_rep(P))]);
+    });
+}
+
 // Deviation forms: the reference density of each population a cell writes,
 // the previous-step density of the cell that reads it (rd[a][i]; the cell
 // itself for the rest population and behind solid cells), from `mac`.
@@ -435,7 +470,7 @@ __device__ __forceinline__ void reader_refs(const WarpNbr &wn, const float4 *mac
         const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
         const float4 m = gather ? __ldg(mac + mb + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
         rdst[0][D] = solid_n ? own[0] : m.x;
-        if (NC == 2) rdst[1][D] = solid_n ? own[1] : m.z;
+        if (NC == 2) rdst[1][D] = solid_n ? own[1] : m.y;
     });
 }
 
@@ -462,6 +497,75 @@ struct Moments {
         }
     }
 };
+
+// ---- component pairs --------------------------------------------------------
+// The two components' values side by side in a float2, computed with the
+// paired FP32 instructions of sm_100 and later: one instruction, two
+// results, each rounded as the scalar operation would be.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
+}
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sel2(bool p, float2 a, float2 b) { return p ? a : b; }
+
+// Weight class of a velocity: 0 rest, 1 axis, 2 diagonal.
+__host__ __device__ constexpr int wclass(int i)
+{
+    return i == 0 ? 0 : ((i <= 4 || i == 9 || i == 14) ? 1 : 2);
+}
+
+// Eqs. 4-5 for both components at once, in the order of Moments.
+struct Moments2 {
+    float2 rho = {0.f, 0.f};
+    float2 j[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+    float2 first = {0.f, 0.f};
+    template <int I>
+    __device__ __forceinline__ void add(float2 v)
+    {
+        rho = add2(rho, v);
+        if constexpr (I == 0) {
+            return;
+        } else if constexpr (rep_of(I) == I) {
+            first = v;
+        } else {
+            constexpr int R = rep_of(I);
+            const float2 d = sub2(first, v);
+            if (cx(R) > 0) j[0] = add2(j[0], d); else if (cx(R) < 0) j[0] = sub2(j[0], d);
+            if (cy(R) > 0) j[1] = add2(j[1], d); else if (cy(R) < 0) j[1] = sub2(j[1], d);
+            if (cz(R) > 0) j[2] = add2(j[2], d); else if (cz(R) < 0) j[2] = sub2(j[2], d);
+        }
+    }
+};
+
+// dev_consume for both components at once: each population is the decoded
+// deviation plus w_I rho_prev (wref, by weight class) or plus the ambient
+// equilibrium (famb, by weight class) for ambient sources.
+template <int ST, class Sink>
+__device__ __forceinline__ void dev_consume2(const DevLoad &L, const float2 wref[3],
+                                             const float2 famb[3], Sink &&sink)
+{
+    auto one = [&]<int I>() {
+        const float2 x = Store<ST>::dec2(L.v[I]);
+        const bool amb = (L.ambs >> I) & 1u;
+        sink.template operator()<I>(add2(x, sel2(amb, famb[wclass(I)], wref[wclass(I)])));
+    };
+    one.template operator()<0>();
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        one.template operator()<pair_rep(P)>();
+        one.template operator()<opp(pair_rep(P))>();
+    });
+}
+
+// First-pass values of a cell as stored in mac: (rho0, rho1, psi0, 0), so
+// that the two densities form one 8-byte pair.
+__device__ __forceinline__ float4 mac_pack(float rho0, float psi0, float rho1)
+{
+    return make_float4(rho0, rho1, psi0, 0.f);
+}
 
 // Eq. 7 (Peng-Robinson) and Eq. 6 (pseudo-potential), FP32.
 __device__ __forceinline__ float psi_of(const KParams &kp, float rho)
@@ -532,8 +636,7 @@ __global__ void __launch_bounds__(CELLS) k_init(KParams kp, const float *in, int
         }
         if constexpr (S::DEV)
             kp.mac[kp.mac_stride + (size_t)slot * CELLS + c] =
-                solid ? make_float4(0.f, 0.f, 0.f, 0.f)
-                      : make_float4(rho_c[0], psi_of(kp, rho_c[0]), rho_c[1], 0.f);
+                solid ? make_float4(0.f, 0.f, 0.f, 0.f) : mac_pack(rho_c[0], psi_of(kp, rho_c[0]), rho_c[1]);
     }
 }
 
@@ -554,7 +657,7 @@ __global__ void __launch_bounds__(THREADS) k_init_dev(KParams kp, int nslots)
         const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
         const bool live = !(bits & 1u);
         const float4 m = __ldg(ref + (size_t)slot * CELLS + c);
-        const float own[2] = {m.x, m.z};
+        const float own[2] = {m.x, m.y};
         float rdst[2][Q];
         reader_refs<NC>(wn, ref, lx, ly, lz, bits, live, own, rdst);
         uint32_t *dst = d_all + (size_t)slot * kp.slot_floats + c;
@@ -605,7 +708,7 @@ __global__ void __launch_bounds__(CELLS) k_ambient_slot(KParams kp)
         base[i * CELLS] = v;
         base[kp.buf_stride + i * CELLS] = v;
     }
-    const float4 m = make_float4(kp.rho_amb[0], psi, kp.rho_amb[1], 0.f);
+    const float4 m = mac_pack(kp.rho_amb[0], psi, kp.rho_amb[1]);
     kp.mac[(size_t)kp.amb_slot * CELLS + c] = m;
     kp.mac[kp.mac_stride + (size_t)kp.amb_slot * CELLS + c] = m;
 }
@@ -632,7 +735,7 @@ __device__ __forceinline__ void macro_cell(const KParams &kp, const WarpNbr &wn,
         u[a][2] = m.j[a][2] * inv;
     }
     if (live) {
-        float4 out = make_float4(rho[0], psi_of(kp, rho[0]), NC == 2 ? rho[1] : 0.f, 0.f);
+        float4 out = mac_pack(rho[0], psi_of(kp, rho[0]), NC == 2 ? rho[1] : 0.f);
         if constexpr (Store<ST>::DEV)
             if ((bits >> HELD_BIT) & 1u) out = prev;
         mac[(size_t)slot * CELLS + c] = out;
@@ -716,6 +819,18 @@ __global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int cri
     }
 }
 
+// Per weight class: w rho_prev (the references of a cell's incoming values)
+// and the ambient equilibrium w rho_amb (the values of ambient sources).
+__device__ __forceinline__ void amb_and_refs(const KParams &kp, float2 ref, float2 wref[3],
+                                             float2 famb[3])
+{
+    Unroll<0, 3>::run([&]<int K>() {
+        constexpr int I = K == 0 ? 0 : (K == 1 ? 1 : 5);
+        wref[K] = mul2(splat(wgt(I)), ref);
+        famb[K] = make_float2(kp.famb[0][I], kp.famb[1][I]);
+    });
+}
+
 // Work items of the deviation-form kernels, software-pipelined: the next
 // item's population loads are issued before the current item is processed,
 // so that they are in flight during its arithmetic.
@@ -725,7 +840,7 @@ struct DevItem {
     uint32_t bits;
     WarpNbr wn;
     DevLoad L;
-    float ref[2];     // the cell's previous density (mac of the other parity)
+    float2 ref;       // the cell's previous densities (mac of the other parity)
 };
 
 template <int ST>
@@ -740,16 +855,14 @@ __device__ __forceinline__ void dev_item(const KParams &kp, const uint32_t *rd, 
     const bool nonsolid = !(bits & 1u);
     const bool held = (bits >> HELD_BIT) & 1u;
     dev_issue<ST>(kp, d.wn, rd, d.slot, d.c, bits, d.ok && nonsolid && !held, false, d.L);
-    float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (d.ok && nonsolid) p = __ldg(mac_prev + (size_t)d.slot * CELLS + d.c);
-    d.ref[0] = p.x;
-    d.ref[1] = p.z;
+    d.ref = make_float2(0.f, 0.f);
+    if (d.ok && nonsolid) d.ref = __ldg(reinterpret_cast<const float2 *>(mac_prev + (size_t)d.slot * CELLS + d.c));
 }
 
 // Pass 1 of a step in the deviation forms (as k_macro).  Held cells keep
 // their density: mac of this step is a copy of the previous one.
 template <int NC, int ST>
-__global__ void __launch_bounds__(THREADS, DEV_MIN_CTAS) k_macro_dev(KParams kp, int step, int criterion)
+__global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KParams kp, int step, int criterion)
 {
     Ctrl *ctrl = kp.ctrl;
     if (criterion && ctrl->status) return;
@@ -783,20 +896,22 @@ __global__ void __launch_bounds__(THREADS, DEV_MIN_CTAS) k_macro_dev(KParams kp,
         if (cur.ok) {
             const bool live = !(cur.bits & 1u);
             const bool held = (cur.bits >> HELD_BIT) & 1u;
-            Moments m;
-            dev_consume<NC, ST>(kp, cur.L, cur.ref, [&]<int I>(int a, float v) { m.template add<I>(a, v); });
+            float2 wref[3], famb[3];
+            amb_and_refs(kp, cur.ref, wref, famb);
+            Moments2 m;
+            dev_consume2<ST>(cur.L, wref, famb, [&]<int I>(float2 v) { m.template add<I>(v); });
+            const float2 inv = make_float2(1.f / m.rho.x, 1.f / m.rho.y);
             float u[2][3];
 #pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const float inv = 1.f / m.rho[a];
-                u[a][0] = m.j[a][0] * inv;
-                u[a][1] = m.j[a][1] * inv;
-                u[a][2] = m.j[a][2] * inv;
+            for (int d = 0; d < 3; ++d) {
+                const float2 ud = mul2(m.j[d], inv);
+                u[0][d] = ud.x;
+                u[1][d] = ud.y;
             }
             if (live)
                 mac[(size_t)cur.slot * CELLS + cur.c] =
-                    held ? make_float4(cur.ref[0], psi_of(kp, cur.ref[0]), cur.ref[1], 0.f)
-                         : make_float4(m.rho[0], psi_of(kp, m.rho[0]), NC == 2 ? m.rho[1] : 0.f, 0.f);
+                    held ? mac_pack(cur.ref.x, psi_of(kp, cur.ref.x), cur.ref.y)
+                         : mac_pack(m.rho.x, psi_of(kp, m.rho.x), NC == 2 ? m.rho.y : 0.f);
             if (criterion) criterion_mark<NC>(kp, ctrl, par, n, cur.slot, cur.c, cur.wn, live && !held, u);
         }
         cur = nxt;
@@ -872,7 +987,7 @@ __global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
         if ((threadIdx.x & 31) == 0 && fluid)
             atomicAdd(&ctrl->fluid_active, (unsigned long long)__popc(fluid));
         const WarpNbr wn = warp_nbr(kp, gid, slot, n_old, true);
-        const float4 amb = make_float4(kp.rho_amb[0], kp.psi_amb, kp.rho_amb[1], 0.f);
+        const float4 amb = mac_pack(kp.rho_amb[0], kp.psi_amb, kp.rho_amb[1]);
         if constexpr (!S::DEV) {
 #pragma unroll
             for (int a = 0; a < NC; ++a) {
@@ -921,7 +1036,7 @@ __device__ __forceinline__ void forces(const KParams &kp, const WarpNbr &wn, uin
                                        bool live, const float rho[2], float F[2][3],
                                        float rdst[2][Q] = nullptr)
 {
-    const float psi_c = live ? kp.mac[(size_t)moff + (size_t)slot * CELLS + c].y : 0.f;
+    const float psi_c = live ? kp.mac[(size_t)moff + (size_t)slot * CELLS + c].z : 0.f;
     const float r0c = rho[0], r1c = NC == 2 ? rho[1] : 0.f;
     float sp[3] = {0, 0, 0}, sp2[3] = {0, 0, 0}, sr0[3] = {0, 0, 0}, sr1[3] = {0, 0, 0},
           ss[3] = {0, 0, 0};
@@ -936,9 +1051,9 @@ __device__ __forceinline__ void forces(const KParams &kp, const WarpNbr &wn, uin
             const uint32_t mb = __shfl_sync(FULL, wn.mbase, k);
             const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
             const float4 m = live ? __ldg(kp.mac + mb + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
-            psi_n[H] = solid_n ? psi_c : m.y;
+            psi_n[H] = solid_n ? psi_c : m.z;
             r0_n[H] = solid_n ? r0c : m.x;
-            r1_n[H] = solid_n ? r1c : m.z;
+            r1_n[H] = solid_n ? r1c : m.y;
             s_n[H] = solid_n ? 1.f : 0.f;
             if constexpr (REFS) {
                 rdst[0][D] = r0_n[H];
@@ -1075,13 +1190,234 @@ __global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
     }
 }
 
-// Pass 2 of a step in the deviation forms (as k_collide, software-pipelined
-// like k_macro_dev).  Every value is stored against the density its reader
-// has now: the neighbour's mac of this step, the cell's own behind a solid
-// cell and for the rest population.  Held cells write their constant
-// equilibrium (density from mac, velocity from uprev).
+// forces() for both components at once (same terms, paired arithmetic):
+// F[d] = (F_0, F_1) along axis d.  The mac copy in use starts at kp.mac +
+// moff.  All lanes must call; `live` masks the loads.
+template <int NC>
+__device__ __forceinline__ void forces2(const KParams &kp, const WarpNbr &wn, uint32_t moff, int slot,
+                                        int c, int lx, int ly, int lz, uint32_t bits, bool live,
+                                        float2 rho, float2 F[3])
+{
+    const float psi_c = live ? kp.mac[(size_t)moff + (size_t)slot * CELLS + c].z : 0.f;
+    const float2 pc = make_float2(psi_c, psi_c * psi_c);
+    float2 sr[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // (sum w rho0 e, sum w rho1 e)
+    float2 sp[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};  // (sum w psi e, sum w psi^2 e)
+    float ss[3] = {0.f, 0.f, 0.f};                        // sum w s e
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        constexpr int I = pair_rep(P);
+        constexpr int J = opp(I);
+        float2 r_n[2], p_n[2];
+        float s_n[2];
+        Unroll<0, 2>::run([&]<int H>() {
+            constexpr int D = H == 0 ? I : J;
+            const int tx = lx + cx(D), ty = ly + cy(D), tz = lz + cz(D);
+            const int k = nbk(tx, ty, tz), lc = lcell(tx, ty, tz);
+            const uint32_t mb = __shfl_sync(FULL, wn.mbase, k);
+            const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
+            const float4 m = live ? __ldg(kp.mac + mb + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
+            r_n[H] = sel2(solid_n, rho, make_float2(m.x, m.y));
+            p_n[H] = sel2(solid_n, pc, make_float2(m.z, m.z * m.z));
+            s_n[H] = solid_n ? 1.f : 0.f;
+        });
+        const float2 w = splat(wgt(I));
+        const float2 dr = mul2(w, sub2(r_n[0], r_n[1]));
+        const float2 dp = mul2(w, sub2(p_n[0], p_n[1]));
+        const float ds = wgt(I) * (s_n[0] - s_n[1]);
+        const int e[3] = {cx(I), cy(I), cz(I)};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            if (e[d] > 0) {
+                sr[d] = add2(sr[d], dr); sp[d] = add2(sp[d], dp); ss[d] += ds;
+            } else if (e[d] < 0) {
+                sr[d] = sub2(sr[d], dr); sp[d] = sub2(sp[d], dp); ss[d] -= ds;
+            }
+        }
+    });
+    // cohesion (component 0), cross force, adhesion, gravity
+    const float a1 = -kp.beta * kp.g_self * psi_c;
+    const float a2 = -(1.f - kp.beta) * 0.5f * kp.g_self;
+    const float2 cross = NC == 2 ? make_float2(-kp.g_cross * rho.x, -kp.g_cross * rho.y)
+                                 : make_float2(0.f, 0.f);
+    const float2 ads = make_float2(-kp.g_ads[0] * fmaxf(rho.x - kp.rho_amb[0], 0.f),
+                                   NC == 2 ? -kp.g_ads[1] * fmaxf(rho.y - kp.rho_amb[1], 0.f) : 0.f);
+    const float2 buoy = make_float2(rho.x - kp.rho_ref[0], NC == 2 ? rho.y - kp.rho_ref[1] : 0.f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float2 coh = make_float2(a1 * sp[d].x + a2 * sp[d].y, 0.f);
+        const float2 swapped = make_float2(sr[d].y, sr[d].x);  // the other component's sum
+        F[d] = fma2(cross, swapped, fma2(ads, splat(ss[d]), fma2(buoy, splat(kp.grav[d]), coh)));
+    }
+}
+
+// Shared by the paired collision kernels: e . a for a velocity vector a
+// given with its negation na (no arithmetic for a single nonzero
+// component).
+template <int I>
+__device__ __forceinline__ float2 edot(const float2 *a, const float2 *na)
+{
+    float2 r = make_float2(0.f, 0.f);
+    bool any = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const int e = d == 0 ? cx(I) : (d == 1 ? cy(I) : cz(I));
+        if (e == 0) continue;
+        const float2 t = e > 0 ? a[d] : na[d];
+        r = any ? add2(r, t) : t;
+        any = true;
+    }
+    return r;
+}
+
+// Pass 1 of a step, FP32 form with two components, paired arithmetic (as
+// k_macro).
+__global__ void __launch_bounds__(THREADS, 4) k_macro2(KParams kp, int step, int criterion)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (criterion && ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+        }
+        const bool live = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
+        Moments2 m;
+        pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live,
+                  [&]<int I>(float2 v) { m.template add<I>(v); });
+        const float2 inv = make_float2(1.f / m.rho.x, 1.f / m.rho.y);
+        float u[2][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float2 ud = mul2(m.j[d], inv);
+            u[0][d] = ud.x;
+            u[1][d] = ud.y;
+        }
+        if (live) kp.mac[(size_t)slot * CELLS + c] = mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y);
+        if (criterion) criterion_mark<2>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
+    }
+}
+
+// Pass 2 of a step, FP32 form with two components, paired arithmetic (as
+// k_collide).
+template <bool TAU1>
+__global__ void __launch_bounds__(THREADS) k_collide2(KParams kp, int step)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par ^ 1];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 7)) return;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;
+    float *wr = kp.f + (size_t)(par ^ 1) * kp.buf_stride;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->cell_updates += (unsigned long long)n * CELLS;
+        ctrl->fluid_updates += ctrl->fluid_active;
+    }
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+        }
+        const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) continue;
+        Moments2 m;
+        float2 fin[TAU1 ? 1 : Q];
+        pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live, [&]<int I>(float2 v) {
+            m.template add<I>(v);
+            if constexpr (!TAU1) fin[I] = v;
+        });
+        const float2 rho = m.rho;
+        const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+        float2 u[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
+        float2 F[3];
+        forces2<2>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
+        if (!live) continue;
+        float2 v[3], nv[3], nu[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            v[d] = fma2(F[d], inv, u[d]);
+            nv[d] = sub2(make_float2(0.f, 0.f), v[d]);
+            nu[d] = sub2(make_float2(0.f, 0.f), u[d]);
+        }
+        const float2 one = splat(1.f);
+        const float2 cv = fma2(splat(-1.5f), fma2(v[0], v[0], fma2(v[1], v[1], mul2(v[2], v[2]))), one);
+        const float2 cu = fma2(splat(-1.5f), fma2(u[0], u[0], fma2(u[1], u[1], mul2(u[2], u[2]))), one);
+        float2 wrho[3];
+        Unroll<0, 3>::run([&]<int K>() {
+            constexpr int I = K == 0 ? 0 : (K == 1 ? 1 : 5);
+            wrho[K] = mul2(splat(wgt(I)), rho);
+        });
+        const float2 relax = splat(1.f - kp.omega);
+        float2 moving = make_float2(0.f, 0.f);
+        float *d0 = wr + (size_t)slot * kp.slot_floats + c;
+        float *d1 = d0 + Q * CELLS;
+        // the 18 moving populations (Eqs. 10-12); the rest population from
+        // the mass balance sum_i f_i = rho (see k_collide)
+        Unroll<1, Q>::run([&]<int I>() {
+            const float2 ev = edot<I>(v, nv);
+            float2 f = mul2(wrho[wclass(I)], fma2(ev, fma2(ev, splat(4.5f), splat(3.f)), cv));
+            if constexpr (!TAU1) {
+                const float2 eu = edot<I>(u, nu);
+                const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
+                f = fma2(relax, sub2(fin[I], e0), f);
+            }
+            moving = add2(moving, f);
+            d0[I * CELLS] = f.x;
+            d1[I * CELLS] = f.y;
+        });
+        const float2 rest = sub2(rho, moving);
+        d0[0] = rest.x;
+        d1[0] = rest.y;
+        (void)cu;
+        if (kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+            float *up = kp.uprev + (size_t)slot * 2 * 3 * CELLS + c;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                up[d * CELLS] = u[d].x;
+                up[(3 + d) * CELLS] = u[d].y;
+            }
+        }
+    }
+}
+
+// Pass 2 of a step in the deviation forms (as k_collide, paired arithmetic
+// for the two components).  Every value
+// is stored against the density its reader has now: the neighbour's mac of
+// this step, the cell's own behind a solid cell and for the rest
+// population.  Held cells write their constant equilibrium (density from
+// mac, velocity from uprev).  With one component the second half of each
+// word carries a dummy unit-density state.
 template <int NC, bool TAU1, int ST>
-__global__ void __launch_bounds__(THREADS, DEV_MIN_CTAS) k_collide_dev(KParams kp, int step)
+__global__ void __launch_bounds__(THREADS, DEV_COLLIDE_MIN_CTAS) k_collide_dev(KParams kp, int step)
 {
     using S = Store<ST>;
     Ctrl *ctrl = kp.ctrl;
@@ -1093,30 +1429,23 @@ __global__ void __launch_bounds__(THREADS, DEV_MIN_CTAS) k_collide_dev(KParams k
     uint32_t *wr = pops<ST>(kp) + (size_t)(par ^ 1) * kp.buf_stride;
     const uint32_t moff = (uint32_t)(par * kp.mac_stride);
     const float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
+    const float2 *mac2 = reinterpret_cast<const float2 *>(kp.mac);  // (rho0, rho1) at 2 i
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->cell_updates += (unsigned long long)n * CELLS;
         ctrl->fluid_updates += ctrl->fluid_active;
     }
     const int total = n * PARTS;
-    const int G = gridDim.x;
     int it = blockIdx.x;
-    if (it >= total) return;
-    DevItem cur;
-    dev_item<ST>(kp, rd, mac_prev, it, nbr_row_lane(kp, it / PARTS),
-                 kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x], moff, cur);
-    int it2 = it + G;
-    int row2 = it2 < total ? nbr_row_lane(kp, it2 / PARTS) : SOLIDBLK;
-    uint32_t bits2 =
-        it2 < total ? kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x] : 1u;
-    for (; it < total; it += G) {
-        DevItem nxt;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        DevItem cur;
+        dev_item<ST>(kp, rd, mac_prev, it, next_row, next_bits, moff, cur);
+        const int it2 = it + gridDim.x;
         if (it2 < total) {
-            dev_item<ST>(kp, rd, mac_prev, it2, row2, bits2, moff, nxt);
-            const int it3 = it2 + G;
-            if (it3 < total) {
-                row2 = nbr_row_lane(kp, it3 / PARTS);
-                bits2 = kp.nbits[(size_t)(it3 / PARTS) * CELLS + (it3 % PARTS) * THREADS + threadIdx.x];
-            }
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
         if (cur.ok) {
             const int slot = cur.slot, c = cur.c;
@@ -1125,87 +1454,86 @@ __global__ void __launch_bounds__(THREADS, DEV_MIN_CTAS) k_collide_dev(KParams k
             const bool nonsolid = !(bits & 1u);
             const bool held = (bits >> HELD_BIT) & 1u;
             const bool live = nonsolid && !held;
-            Moments m;
-            float fin[TAU1 ? 1 : NC][Q];
-            dev_consume<NC, ST>(kp, cur.L, cur.ref, [&]<int I>(int a, float v) {
-                m.template add<I>(a, v);
-                if constexpr (!TAU1) fin[a][I] = v;
+            float2 wref[3], famb[3];
+            amb_and_refs(kp, cur.ref, wref, famb);
+            Moments2 m;
+            float2 fin[TAU1 ? 1 : Q];
+            dev_consume2<ST>(cur.L, wref, famb, [&]<int I>(float2 v) {
+                m.template add<I>(v);
+                if constexpr (!TAU1) fin[I] = v;
             });
-            float rho[2] = {m.rho[0], m.rho[1]}, u[2][3];
+            float2 rho = m.rho;
+            if (NC == 1) rho.y = 1.f;
+            float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+            float2 u[3];
 #pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const float inv = 1.f / rho[a];
-                u[a][0] = m.j[a][0] * inv;
-                u[a][1] = m.j[a][1] * inv;
-                u[a][2] = m.j[a][2] * inv;
-                if (held) {
-                    const float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
-                    rho[a] = cur.ref[a];
-                    u[a][0] = up[0];
-                    u[a][1] = up[CELLS];
-                    u[a][2] = up[2 * CELLS];
-                }
-            }
-            float F[2][3];
-            forces<NC>(kp, cur.wn, moff, slot, c, lx, ly, lz, bits, nonsolid, rho, F);
-            // every lane runs the collision (its shuffles need the whole
-            // warp); solid cells store nothing
-            float vx[2], vy[2], vz[2], vv[2], uu[2], moving[2] = {0.f, 0.f};
+            for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
+            if (held) {
+                rho = cur.ref;
+                if (NC == 1) rho.y = 1.f;
+                const float *up = kp.uprev + (size_t)slot * NC * 3 * CELLS + c;
 #pragma unroll
-            for (int a = 0; a < NC; ++a) {
-                const float inv = held ? 0.f : 1.f / rho[a];
-                vx[a] = u[a][0] + F[a][0] * inv;
-                vy[a] = u[a][1] + F[a][1] * inv;
-                vz[a] = u[a][2] + F[a][2] * inv;
-                vv[a] = vx[a] * vx[a] + vy[a] * vy[a] + vz[a] * vz[a];
-                uu[a] = u[a][0] * u[a][0] + u[a][1] * u[a][1] + u[a][2] * u[a][2];
+                for (int d = 0; d < 3; ++d)
+                    u[d] = make_float2(up[d * CELLS], NC == 2 ? up[(3 + d) * CELLS] : 0.f);
+                inv = make_float2(0.f, 0.f);  // no force term
             }
+            if (NC == 1)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) u[d].y = 0.f;
+            float2 F[3];
+            forces2<NC>(kp, cur.wn, moff, slot, c, lx, ly, lz, bits, nonsolid, rho, F);
+            // Eqs. 10-12 with tau = 1 (f* = f_eq(rho, u + F / rho)), else
+            // f* = f_eq(rho, u + F / rho) + (1 - 1/tau) (f - f_eq(rho, u));
+            // every lane runs it (its shuffles need the whole warp), solid
+            // cells store nothing
+            float2 v[3], nv[3], nu[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                v[d] = fma2(F[d], inv, u[d]);
+                nv[d] = sub2(make_float2(0.f, 0.f), v[d]);
+                nu[d] = sub2(make_float2(0.f, 0.f), u[d]);
+            }
+            const float2 one = splat(1.f);
+            const float2 cv = fma2(splat(-1.5f), fma2(v[0], v[0], fma2(v[1], v[1], mul2(v[2], v[2]))), one);
+            const float2 cu = fma2(splat(-1.5f), fma2(u[0], u[0], fma2(u[1], u[1], mul2(u[2], u[2]))), one);
+            float2 wrho[3];
+            Unroll<0, 3>::run([&]<int K>() {
+                constexpr int I = K == 0 ? 0 : (K == 1 ? 1 : 5);
+                wrho[K] = mul2(splat(wgt(I)), rho);
+            });
+            const float2 relax = splat(held ? 0.f : 1.f - kp.omega);
+            float2 moving = make_float2(0.f, 0.f);
             uint32_t *dst = wr + (size_t)slot * kp.slot_floats + c;
-            // The 18 moving populations (Eqs. 10-12), each against its
-            // reader's density; the rest population from the mass balance
-            // over the values as their readers will decode them, so that it
-            // absorbs the rounding of the other 18.
             Unroll<1, Q>::run([&]<int I>() {
+                const float2 ev = edot<I>(v, nv);
+                float2 f = mul2(wrho[wclass(I)], fma2(ev, fma2(ev, splat(4.5f), splat(3.f)), cv));
+                if constexpr (!TAU1) {
+                    const float2 eu = edot<I>(u, nu);
+                    const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
+                    f = fma2(relax, sub2(fin[I], e0), f);
+                }
+                moving = add2(moving, f);
+                // the reader's density: the neighbour's, or the cell's own
                 const int tx = lx + cx(I), ty = ly + cy(I), tz = lz + cz(I);
                 const uint32_t mb = __shfl_sync(FULL, cur.wn.mbase, nbk(tx, ty, tz));
                 const bool solid_n = (bits >> opp(I)) & 1u;  // x + e_I = x - e_opp(I)
-                const float4 mr = (solid_n || !nonsolid) ? make_float4(rho[0], 0.f, rho[1], 0.f)
-                                                         : __ldg(kp.mac + mb + lcell(tx, ty, tz));
-                const float rr[2] = {mr.x, mr.z};
-                float d[2] = {0.f, 0.f};
-#pragma unroll
-                for (int a = 0; a < NC; ++a) {
-                    const float wr_ = wgt(I) * rho[a];
-                    float v = feq<I>(wr_, vx[a], vy[a], vz[a], vv[a]);
-                    if constexpr (!TAU1) {
-                        if (!held) {
-                            const float e0 = feq<I>(wr_, u[a][0], u[a][1], u[a][2], uu[a]);
-                            v += (1.f - kp.omega) * (fin[a][I] - e0);
-                        }
-                    }
-                    d[a] = __fmaf_rn(-wgt(I), rr[a], v);
-                }
-                const uint32_t h = S::enc2(d[0], d[1]);
-                if (nonsolid) dst[I * CELLS] = h;
-                const float2 back = S::dec2(h);
-                moving[0] += __fmaf_rn(wgt(I), rr[0], back.x);
-                moving[1] += __fmaf_rn(wgt(I), rr[1], back.y);
+                const float2 rr = (solid_n || !nonsolid) ? rho : __ldg(mac2 + 2 * (mb + lcell(tx, ty, tz)));
+                const float2 d = fma2(splat(-wgt(I)), rr, f);
+                if (nonsolid) dst[I * CELLS] = S::enc2(d.x, d.y);
             });
-            if (nonsolid)
-                dst[0] = S::enc2(__fmaf_rn(-wgt(0), rho[0], rho[0] - moving[0]),
-                                 NC == 2 ? __fmaf_rn(-wgt(0), rho[1], rho[1] - moving[1]) : 0.f);
+            // rest population from the mass balance sum_i f_i = rho
+            const float2 d0 = fma2(splat(-wgt(0)), rho, sub2(rho, moving));
+            if (nonsolid) dst[0] = S::enc2(d0.x, d0.y);
+            (void)cu;
             if (live && kp.progressive && (reach_bits(lx, ly, lz) & cur.wn.amb)) {
+                float *up = kp.uprev + (size_t)slot * NC * 3 * CELLS + c;
 #pragma unroll
-                for (int a = 0; a < NC; ++a) {
-                    float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
-                    up[0] = u[a][0];
-                    up[CELLS] = u[a][1];
-                    up[2 * CELLS] = u[a][2];
+                for (int d = 0; d < 3; ++d) {
+                    up[d * CELLS] = u[d].x;
+                    if (NC == 2) up[(3 + d) * CELLS] = u[d].y;
                 }
             }
         }
-        cur = nxt;
-        it2 += G;
     }
 }
 
@@ -1235,7 +1563,7 @@ __global__ void __launch_bounds__(THREADS) k_output(KParams kp, int rdbuf, int c
             if (live) {
                 const float4 p = __ldg(mac_prev + (size_t)slot * CELLS + c);
                 ref[0] = p.x;
-                ref[1] = p.z;
+                ref[1] = p.y;
             }
         }
         Moments m;
@@ -1288,7 +1616,7 @@ __device__ __forceinline__ void stored_cell(const KParams &kp, int rdbuf, int sl
         const float4 *mref = kp.mac + (size_t)(rdbuf ^ 1) * kp.mac_stride;
         const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
         const float4 m = live ? __ldg(mref + (size_t)slot * CELLS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float own[2] = {m.x, m.z};
+        const float own[2] = {m.x, m.y};
         reader_refs<2>(wn, mref, c & 7, (c >> 3) & 7, c >> 6, bits, live, own, rdst);
     }
     if constexpr (S::DEV) {
@@ -1408,7 +1736,7 @@ struct Launch {
             if (kp.ncomp == 2) return launch_persistent<k_macro_dev<2, ST>>(sms, s, kp, step, criterion);
             return launch_persistent<k_macro_dev<1, ST>>(sms, s, kp, step, criterion);
         } else {
-            if (kp.ncomp == 2) return launch_persistent<k_macro<2>>(sms, s, kp, step, criterion);
+            if (kp.ncomp == 2) return launch_persistent<k_macro2>(sms, s, kp, step, criterion);
             return launch_persistent<k_macro<1>>(sms, s, kp, step, criterion);
         }
     }
@@ -1432,8 +1760,8 @@ struct Launch {
             return launch_persistent<k_collide_dev<1, false, ST>>(sms, s, kp, step);
         } else {
             if (kp.ncomp == 2) {
-                if (tau1) return launch_persistent<k_collide<2, true>>(sms, s, kp, step);
-                return launch_persistent<k_collide<2, false>>(sms, s, kp, step);
+                if (tau1) return launch_persistent<k_collide2<true>>(sms, s, kp, step);
+                return launch_persistent<k_collide2<false>>(sms, s, kp, step);
             }
             if (tau1) return launch_persistent<k_collide<1, true>>(sms, s, kp, step);
             return launch_persistent<k_collide<1, false>>(sms, s, kp, step);
@@ -1467,8 +1795,8 @@ struct Launch {
             a = occupancy<k_collide_dev<2, true, ST>>();
             b = occupancy<k_macro_dev<2, ST>>();
         } else {
-            a = occupancy<k_collide<2, true>>();
-            b = occupancy<k_macro<2>>();
+            a = occupancy<k_collide2<true>>();
+            b = occupancy<k_macro2>();
         }
         return a < b ? a : b;
     }
