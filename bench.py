@@ -138,9 +138,13 @@ def make_case(S=None, size=256):
     return W.porous_injection(**kw)
 
 
-def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32"):
-    """Warm up, then time `steps` steps one by one (L2 flushed before each)."""
+def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32", proposer=None):
+    """Warm up, then time `steps` steps one by one (L2 flushed before each).
+    proposer: an lbm MLP to run the activation proposer with (period 16,
+    threshold 0.5)."""
     sim = L.from_case(case, progressive=progressive, storage=storage)
+    if proposer is not None:
+        sim.set_proposer(proposer, period=16, threshold=0.5)
     sim.step(warmup)
     stream = torch.cuda.current_stream()
     st0 = sim.stats()
@@ -167,6 +171,9 @@ def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="
         kernel_ms=[b - a for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
         kernel_launches=[b - a for a, b in zip(st0["kernel_launches"], st1["kernel_launches"])],
         active_end=st1["active_blocks"],
+        created=st1["created_blocks"] - st0["created_blocks"],
+        prepared=st1["prepared_blocks"] - st0["prepared_blocks"],
+        prepared_hits=st1["prepared_hits"] - st0["prepared_hits"],
         nonsolid_blocks=st1["nonsolid_blocks"],
         total_blocks=st1["total_blocks"],
         clocks=clk.summary(),
@@ -277,6 +284,8 @@ def main():
                     help="time the static mesh only (profiling captures)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="population storage form (arithmetic is FP32 in all)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip timing the FP16, BF16 and learned-proposer forms")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -317,6 +326,25 @@ def main():
     if not args.no_static:
         stat = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage)
         s_max, s_cells = reduce_max_sum(dist, torch, stat["ms"], stat["cells"])
+    forms = {}
+    if not args.no_forms and args.storage == "fp32":
+        from paper_1510_03560_gb300 import proposer as PR
+        for form in ("fp16", "bf16"):
+            r = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, form)
+            f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
+            forms[form] = {"mlups": round(f_cells / (f_max * 1e-3) / 1e6, 1),
+                           "active_fraction_end": round(r["active_end"] / r["total_blocks"], 4),
+                           "collide_ms_per_step": round(r["kernel_ms"][2] / args.steps, 5)}
+        mlp = PR.load_model(L)
+        r = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, "fp32", proposer=mlp)
+        f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
+        forms["learned"] = {
+            "mlups": round(f_cells / (f_max * 1e-3) / 1e6, 1),
+            "created": r["created"], "prepared": r["prepared"], "prepared_hits": r["prepared_hits"],
+            "activate_ms_per_step": round(r["kernel_ms"][1] / args.steps, 5),
+            "activate_ms_per_step_without": round(prog["kernel_ms"][1] / args.steps, 5),
+            "period": 16, "threshold": 0.5, "inference": "bf16 operands, fp32 accumulation"}
+        mlp.close()
     e2e = None if args.no_e2e else run_e2e(L, torch, case, args.warmup + args.steps, args.storage)
     if e2e is not None:
         e_max, e_cells = reduce_max_sum(dist, torch, e2e["wall"], e2e["cells"])
@@ -362,6 +390,9 @@ def main():
         "l2": "256 MiB buffer written before every timed step; flush outside the timed events",
         "parallelism": f"replicas x{world}",
     }
+    if forms:
+        forms["fp32_progressive_mlups"] = round(mlups, 1)
+        config["forms"] = forms
     if stat is not None:
         s_mlups = s_cells / (s_max * 1e-3) / 1e6
         config["static_mlups"] = round(s_mlups, 1)

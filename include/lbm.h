@@ -118,6 +118,9 @@ typedef struct lbm_stats {
                                    (0 stream+macro, 1 block creation, 2 force+collide,
                                    3 other) accumulated over lbm_step calls */
     long long kernel_launches[4];
+    long long created_blocks;   /* blocks created by the criterion since lbm_set_geometry */
+    long long prepared_blocks;  /* blocks the activation proposer prepared */
+    long long prepared_hits;    /* created blocks that had been prepared */
 } lbm_stats;
 
 /* Validate `p`, allocate the block pool (capacity x 2 buffers x ncomp x 19 x
@@ -236,6 +239,79 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * lbm_last_error(NULL)). */
 int lbm_mass_noalloc(const float *f, const uint32_t *solid, long long nblocks, int ncomp,
                      double *mass, void *stream);
+
+
+/* ---- learned activation proposer ------------------------------------------
+ * Not part of the paper.  A small network predicts which unmeshed blocks the
+ * criterion of Eq. 13 will create within the next steps; on a side stream
+ * the context then prepares those blocks' per-cell solid words ahead of
+ * time, work block creation would otherwise do when the block is created.
+ * The criterion alone decides which blocks are created, and a prepared word
+ * equals the one computed at creation, so results are bit-identical with
+ * and without the proposer; a block that was not predicted is prepared at
+ * creation as before.
+ *
+ * Features of a frontier block (an unmeshed block that is not all solid and
+ * has a meshed face or edge neighbour), LBM_MLP_IN = 34 values:
+ *   [0..1]   mean density of components 0 and 1 over the cells of its
+ *            meshed face neighbours that touch it (rho_amb when none)
+ *   [2..7]   mass flux into it through faces -x, +x, -y, +y, -z, +z: the
+ *            sum over the touching cells of the neighbour of (j_0 + j_1) . n,
+ *            n the unit normal into the block, j the momentum of Eq. 5 (0
+ *            for an unmeshed neighbour)
+ *   [8..33]  1 when the neighbour block (dx, dy, dz), dx fastest, skipping
+ *            the block itself, is meshed, else 0
+ * Moments are those of the next streaming of the current populations. */
+#define LBM_MLP_IN 34
+#define LBM_MLP_HIDDEN 64
+/* parameters, packed: W1 [34][64], b1 [64], W2 [64][64], b2 [64], w3 [64], b3 */
+#define LBM_MLP_NPARAM (LBM_MLP_IN * LBM_MLP_HIDDEN + LBM_MLP_HIDDEN + \
+                        LBM_MLP_HIDDEN * LBM_MLP_HIDDEN + LBM_MLP_HIDDEN + LBM_MLP_HIDDEN + 1)
+
+/* Frontier blocks of the current state, ascending, and their features:
+ * blocks [cap] int32, feat [cap][LBM_MLP_IN] (host arrays; either may be
+ * NULL when cap is 0); *n receives the count (which may exceed cap). */
+int lbm_frontier_features(lbm_ctx *ctx, int32_t *blocks, float *feat, long long cap,
+                          long long *n);
+
+/* Step at which each block was meshed: 0 for the initial blocks, t + 1 for
+ * a block created by the criterion in step t (0-based), -1 for blocks not
+ * meshed.  out: host array of nx/8 * ny/8 * nz/8 int32. */
+int lbm_activation_steps(lbm_ctx *ctx, int32_t *out);
+
+/* A multilayer perceptron LBM_MLP_IN -> 64 -> 64 -> 1 (ReLU, ReLU,
+ * logistic output) with its own device memory, trained with the binary
+ * cross-entropy.  Inputs are standardised inside: x' = (x - mean) * scale. */
+typedef struct lbm_mlp lbm_mlp;
+
+/* max_batch: the largest n of the calls below; stream: cudaStream_t (NULL =
+ * default) for every launch.  Parameters start at zero, mean 0, scale 1. */
+int lbm_mlp_create(int max_batch, void *stream, lbm_mlp **out);
+int lbm_mlp_destroy(lbm_mlp *mlp);
+/* params: host array of LBM_MLP_NPARAM floats, packed as above */
+int lbm_mlp_set_params(lbm_mlp *mlp, const float *params);
+int lbm_mlp_get_params(lbm_mlp *mlp, float *params);
+/* mean, scale: host arrays of LBM_MLP_IN floats */
+int lbm_mlp_set_scaling(lbm_mlp *mlp, const float *mean, const float *scale);
+/* Probabilities prob[n] (device) of the n raw feature rows x [n][34]
+ * (device).  bf16 = 1: inputs, hidden activations and weights rounded to
+ * bfloat16, products accumulated in FP32; 0: FP32 throughout. */
+int lbm_mlp_forward(lbm_mlp *mlp, const float *x, int n, int bf16, float *prob);
+/* FP32 forward and backward pass over n rows x [n][34], labels y [n] (0 or
+ * 1) (device): the mean loss to *loss (host) and its gradient with respect
+ * to the parameters, kept for lbm_mlp_adam and copied to grad (host,
+ * LBM_MLP_NPARAM floats) when grad is not NULL.  Every sum runs in a fixed
+ * order, so the result does not depend on scheduling. */
+int lbm_mlp_loss_grad(lbm_mlp *mlp, const float *x, const float *y, int n, double *loss,
+                      float *grad);
+/* One Adam update (step count t >= 1) with the last gradient. */
+int lbm_mlp_adam(lbm_mlp *mlp, float lr, float beta1, float beta2, float eps, int t);
+
+/* Use `mlp` (not owned; NULL turns the proposer off) every `period` steps
+ * of lbm_step / lbm_step_async: frontier blocks whose probability (BF16
+ * inference) exceeds `threshold` are prepared on a side stream.  The mlp
+ * must outlive its use by the context.  Progressive mode only. */
+int lbm_set_proposer(lbm_ctx *ctx, lbm_mlp *mlp, int period, float threshold);
 
 #ifdef __cplusplus
 }

@@ -73,6 +73,20 @@ struct lbm_ctx {
     std::vector<cudaEvent_t> event_pool;
     double kernel_ms[4] = {0, 0, 0, 0};
     long long kernel_launches[4] = {0, 0, 0, 0};
+    // frontier features and the activation proposer
+    unsigned *pmark = nullptr;   // [nblocks]
+    int *plist = nullptr;        // [nblocks]
+    int *pcount = nullptr;       // [1]
+    int *pnsnap = nullptr;       // [1]: meshed count taken between two steps
+    float *pfeat = nullptr;      // [nblocks][LBM_MLP_IN]
+    float *pprob = nullptr;      // [nblocks]
+    unsigned *prep = nullptr;    // [nblocks]
+    uint32_t *nbits_pre = nullptr;  // [nblocks][CELLS]
+    lbm_mlp *mlp = nullptr;
+    int period = 0;
+    float threshold = 0.5f;
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_ev = nullptr;
 };
 
 namespace {
@@ -266,10 +280,36 @@ int read_ctrl(lbm_ctx *c, Ctrl &out)
     return LBM_OK;
 }
 
+// One round of the activation proposer before step t, on the side stream:
+// frontier blocks, their features, the network, the preparation of the
+// blocks it selects.  The meshed count is copied on the main stream first,
+// so the side stream only reads table rows that are complete.
+int enqueue_proposer(lbm_ctx *c, int t)
+{
+    KParams &k = c->kp;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->pnsnap, &k.ctrl->n_active[t & 1], sizeof(int),
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    CUDA_OR_FAIL(c, cudaEventRecord(c->side_ev, c->stream));
+    CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->side, c->side_ev, 0));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->pmark, 0, c->nblocks * sizeof(unsigned), c->side));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->pcount, 0, sizeof(int), c->side));
+    CUDA_OR_FAIL(c, launch_frontier(k, c->pnsnap, c->pmark, c->plist, c->pcount, c->sms, c->side));
+    CUDA_OR_FAIL(c, launch_features(k, t & 1, c->pnsnap, c->plist, c->pcount, c->pfeat, c->sms, c->side));
+    CUDA_OR_FAIL(c, mlp_forward_on(c->mlp, c->pfeat, (int)c->nblocks, c->pcount, 1, c->pprob, c->side));
+    CUDA_OR_FAIL(c, launch_prepare(k, c->plist, c->pcount, c->pprob, c->threshold, c->prep, c->nbits_pre,
+                                   c->sms, c->side));
+    c->launches += 4;
+    return LBM_OK;
+}
+
 int enqueue_steps(lbm_ctx *c, int nsteps)
 {
     for (int k = 0; k < nsteps; ++k) {
         const int t = (int)(c->step + k);
+        if (c->mlp && t % c->period == 0) {
+            int rc = enqueue_proposer(c, t);
+            if (rc) return rc;
+        }
         CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
                          return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
                      }));
@@ -284,6 +324,7 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
 
 int finish(lbm_ctx *c)
 {
+    if (c->side) CUDA_OR_FAIL(c, cudaStreamSynchronize(c->side));
     Ctrl ctrl;
     int rc = read_ctrl(c, ctrl);
     if (rc) return rc;
@@ -377,6 +418,7 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
         {(void **)&k.held, (size_t)c->nblocks * MASK_WORDS * sizeof(uint32_t)},
         {(void **)&k.cand_list, (size_t)c->nblocks * sizeof(int)},
         {(void **)&k.cand_mark, (size_t)c->nblocks * sizeof(unsigned)},
+        {(void **)&k.act_step, (size_t)c->nblocks * sizeof(int)},
         {(void **)&k.ctrl, sizeof(Ctrl)},
         {(void **)&c->mass_partial, (size_t)c->capacity * 2 * sizeof(double)},
         {(void **)&c->mass_out, 2 * sizeof(double)},
@@ -414,9 +456,12 @@ int lbm_destroy(lbm_ctx *c)
 {
     if (!c) return LBM_OK;
     DeviceGuard g(c->device);
+    if (c->side) cudaStreamSynchronize(c->side);
     cudaStreamSynchronize(c->stream);
     flush_profile(c);
     free_all(c);
+    if (c->side_ev) cudaEventDestroy(c->side_ev);
+    if (c->side) cudaStreamDestroy(c->side);
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     delete c;
@@ -431,6 +476,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
         return fail(c, LBM_EINVAL, "cell_type, rho_init and rho_amb are required");
     DeviceGuard g(c->device);
     if (!g.ok) return fail(c, LBM_ECUDA, "cannot select device %d", c->device);
+    if (c->side) CUDA_OR_FAIL(c, cudaStreamSynchronize(c->side));
     const lbm_params &p = c->p;
     const long long ncell = (long long)p.nx * p.ny * p.nz;
     const int nc = p.ncomp;
@@ -524,6 +570,13 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.solid, c->solid_h.data(), nb * MASK_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.held, c->held_h.data(), nb * MASK_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemsetAsync(k.cand_mark, 0, nb * sizeof(unsigned), s));
+    {
+        std::vector<int> act(nb, -1);
+        for (int sl = 0; sl < n0; ++sl) act[block_of[sl]] = 0;
+        CUDA_OR_FAIL(c, cudaMemcpyAsync(k.act_step, act.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    }
+    if (c->prep) CUDA_OR_FAIL(c, cudaMemsetAsync(c->prep, 0, nb * sizeof(unsigned), s));
     Ctrl ctrl{};
     ctrl.n_active[0] = ctrl.n_active[1] = n0;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(k.ctrl, &ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
@@ -759,6 +812,9 @@ int lbm_get_stats(lbm_ctx *c, lbm_stats *out)
         out->active_blocks = ctrl.n_active[c->step & 1];
         out->cell_updates = (long long)ctrl.cell_updates;
         out->fluid_updates = (long long)ctrl.fluid_updates;
+        out->created_blocks = (long long)ctrl.created;
+        out->prepared_blocks = (long long)ctrl.prepared;
+        out->prepared_hits = (long long)ctrl.prepared_hits;
         long long ns = 0;
         for (int v : c->nonsolid_h) ns += v > 0;
         out->nonsolid_blocks = ns;
@@ -767,6 +823,108 @@ int lbm_get_stats(lbm_ctx *c, lbm_stats *out)
         out->kernel_ms[k] = c->kernel_ms[k];
         out->kernel_launches[k] = c->kernel_launches[k];
     }
+    return LBM_OK;
+}
+
+// Buffers of the frontier features (and of the proposer), on first use.
+static int ensure_frontier_buffers(lbm_ctx *c)
+{
+    if (c->pmark) return LBM_OK;
+    const size_t nb = (size_t)c->nblocks;
+    struct {
+        void **dst;
+        size_t bytes;
+    } want[] = {
+        {(void **)&c->pmark, nb * sizeof(unsigned)},  {(void **)&c->plist, nb * sizeof(int)},
+        {(void **)&c->pcount, sizeof(int)},           {(void **)&c->pnsnap, sizeof(int)},
+        {(void **)&c->pfeat, nb * LBM_MLP_IN * sizeof(float)}, {(void **)&c->pprob, nb * sizeof(float)},
+        {(void **)&c->prep, nb * sizeof(unsigned)},   {(void **)&c->nbits_pre, nb * CELLS * sizeof(uint32_t)},
+    };
+    for (auto &w : want) {
+        *w.dst = dev_alloc(c, w.bytes);
+        if (!*w.dst) return fail(c, LBM_ENOMEM, "device allocation of %zu bytes failed", w.bytes);
+    }
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->prep, 0, nb * sizeof(unsigned), c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_frontier_features(lbm_ctx *c, int32_t *blocks, float *feat, long long cap, long long *n)
+{
+    if (!c || !n) return LBM_EINVAL;
+    if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
+    if (cap > 0 && (!blocks || !feat)) return fail(c, LBM_EINVAL, "blocks and feat are required");
+    DeviceGuard g(c->device);
+    int rc = ensure_frontier_buffers(c);
+    if (rc) return rc;
+    if (c->side) CUDA_OR_FAIL(c, cudaStreamSynchronize(c->side));
+    KParams &k = c->kp;
+    cudaStream_t s = c->stream;
+    const int t = (int)c->step;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(c->pnsnap, &k.ctrl->n_active[t & 1], sizeof(int),
+                                    cudaMemcpyDeviceToDevice, s));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->pmark, 0, c->nblocks * sizeof(unsigned), s));
+    CUDA_OR_FAIL(c, cudaMemsetAsync(c->pcount, 0, sizeof(int), s));
+    CUDA_OR_FAIL(c, launch_frontier(k, c->pnsnap, c->pmark, c->plist, c->pcount, c->sms, s));
+    CUDA_OR_FAIL(c, launch_features(k, t & 1, c->pnsnap, c->plist, c->pcount, c->pfeat, c->sms, s));
+    c->launches += 2;
+    int cnt = 0;
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(&cnt, c->pcount, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    *n = cnt;
+    if (cap <= 0 || cnt == 0) return LBM_OK;
+    std::vector<int> list(cnt);
+    std::vector<float> f((size_t)cnt * LBM_MLP_IN);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(list.data(), c->plist, cnt * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(f.data(), c->pfeat, f.size() * sizeof(float), cudaMemcpyDeviceToHost, s));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    std::vector<int> order(cnt);
+    for (int i = 0; i < cnt; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return list[a] < list[b]; });
+    const long long m = std::min<long long>(cap, cnt);
+    for (long long i = 0; i < m; ++i) {
+        blocks[i] = list[order[i]];
+        std::memcpy(feat + i * LBM_MLP_IN, f.data() + (size_t)order[i] * LBM_MLP_IN, LBM_MLP_IN * sizeof(float));
+    }
+    return LBM_OK;
+}
+
+int lbm_activation_steps(lbm_ctx *c, int32_t *out)
+{
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
+    DeviceGuard g(c->device);
+    CUDA_OR_FAIL(c, cudaMemcpyAsync(out, c->kp.act_step, c->nblocks * sizeof(int), cudaMemcpyDeviceToHost,
+                                    c->stream));
+    CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+int lbm_set_proposer(lbm_ctx *c, lbm_mlp *mlp, int period, float threshold)
+{
+    if (!c) return LBM_EINVAL;
+    DeviceGuard g(c->device);
+    if (!mlp) {
+        if (c->side) CUDA_OR_FAIL(c, cudaStreamSynchronize(c->side));
+        c->mlp = nullptr;
+        c->kp.prep = nullptr;
+        c->kp.nbits_pre = nullptr;
+        return LBM_OK;
+    }
+    if (!c->p.progressive) return fail(c, LBM_EINVAL, "the proposer needs the progressive mesh");
+    if (period < 1) return fail(c, LBM_EINVAL, "period must be >= 1");
+    if (!std::isfinite(threshold)) return fail(c, LBM_EINVAL, "threshold must be finite");
+    int rc = ensure_frontier_buffers(c);
+    if (rc) return rc;
+    if (!c->side) {
+        CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->side_ev, cudaEventDisableTiming));
+    }
+    c->mlp = mlp;
+    c->period = period;
+    c->threshold = threshold;
+    c->kp.prep = c->prep;
+    c->kp.nbits_pre = c->nbits_pre;
     return LBM_OK;
 }
 

@@ -31,6 +31,9 @@ struct Ctrl {
     unsigned long long cell_updates;   // 512 x meshed blocks, summed over steps
     unsigned long long fluid_updates;  // fluid cells of meshed blocks, summed over steps
     unsigned long long fluid_active;   // fluid cells of the meshed blocks now
+    unsigned long long created;        // blocks created by the criterion
+    unsigned long long prepared;       // blocks prepared by the activation proposer
+    unsigned long long prepared_hits;  // created blocks that had been prepared
     float psi_amb;     // psi of the ambient density, evaluated on the device
     int check_site;    // checked builds: first failed index check (site id)
     long long check_value;  // and the offending value
@@ -79,6 +82,9 @@ struct KParams {
     const uint32_t *held;   // [nblocks][MASK_WORDS]
     int *cand_list;     // [nblocks]
     unsigned *cand_mark;    // [nblocks]
+    int *act_step;      // [nblocks]: step + 1 of creation, 0 initial, -1 unmeshed
+    const unsigned *prep;       // [nblocks] or NULL: 1 once nbits_pre holds the block's words
+    const uint32_t *nbits_pre;  // [nblocks][CELLS]: solid words prepared by the proposer
     Ctrl *ctrl;
     size_t buf_stride;  // elements (floats or words) per population buffer
     int slot_floats;    // elements per slot: ncomp * Q * CELLS (FP32) or
@@ -99,6 +105,8 @@ struct StorageOps {
     cudaError_t (*output)(const KParams &, int, int, int, int, float *, int, cudaStream_t);
     cudaError_t (*mass_partial)(const KParams &, int, int, double *, int, cudaStream_t);
     cudaError_t (*block_pops)(const KParams &, int, int, float *, cudaStream_t);
+    cudaError_t (*features)(const KParams &, int, const int *, const int *, const int *, float *, int,
+                            cudaStream_t);
     int (*ctas_per_sm)();
 };
 const StorageOps *storage_ops_fp32();
@@ -126,6 +134,22 @@ cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, doubl
 // FP32 populations of one slot of buffer rd into out[ncomp][Q][CELLS] (16-bit forms).
 cudaError_t launch_block_pops(const KParams &kp, int rd, int slot, float *out, cudaStream_t s);
 int max_ctas_per_sm_stream_kernels(int storage);
+
+// Frontier blocks and their features (lbm_kernels.cu; features per storage
+// form).  mark/list: [nblocks] scratch, count: one int (zeroed by the
+// caller with mark); par: the read buffer; nsnap: a device copy of the
+// meshed-block count taken between two steps (only those slots are read).
+cudaError_t launch_frontier(const KParams &kp, const int *nsnap, unsigned *mark, int *list, int *count,
+                            int sms, cudaStream_t s);
+cudaError_t launch_features(const KParams &kp, int par, const int *nsnap, const int *list,
+                            const int *count, float *feat, int sms, cudaStream_t s);
+// Prepare the listed blocks whose probability exceeds thr (side stream).
+cudaError_t launch_prepare(const KParams &kp, const int *list, const int *count, const float *prob,
+                           float thr, unsigned *prep, uint32_t *nbits_pre, int sms, cudaStream_t s);
+// The network's forward pass on a stream (lbm_mlp.cu); the sample count is
+// n, or *ndev when ndev is not NULL.
+cudaError_t mlp_forward_on(const lbm_mlp *m, const float *x, int n, const int *ndev, int bf16,
+                           float *prob, cudaStream_t s);
 
 // Message returned by lbm_last_error(NULL) (lbm_capi.cpp).
 void set_global_error(const char *msg);

@@ -29,6 +29,53 @@ __global__ void __launch_bounds__(1024) k_mass_final(const double *partial, int 
     if (t < 2) out[t] = red[0][t];
 }
 
+// Frontier blocks (unmeshed, not all solid, with a meshed face or edge
+// neighbour) of the first *nsnap slots, each listed once: one warp per
+// slot, one lane per neighbour.
+__global__ void __launch_bounds__(256) k_frontier(KParams kp, const int *nsnap, unsigned *mark, int *list,
+                                                  int *count)
+{
+    const int n = *nsnap;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    const bool face_or_edge = lane < 27 && lane != 13 && (dx * dx + dy * dy + dz * dz) <= 2;
+    for (int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); slot < n; slot += nwarps) {
+        if (!face_or_edge) continue;
+        if (kp.nbr[(size_t)slot * NBR_STRIDE + lane] != AMBIENT) continue;
+        const int nid = neighbour_of(kp, kp.block_of[slot], lane);
+        if (nid >= 0 && atomicCAS(&mark[nid], 0u, 1u) == 0u) list[atomicAdd(count, 1)] = nid;
+    }
+}
+
+// Prepare the listed blocks whose probability exceeds thr: their cells'
+// solid words (as block creation computes them) into nbits_pre, then the
+// flag.  One CTA per block.
+__global__ void __launch_bounds__(CELLS) k_prepare(KParams kp, const int *list, const int *count,
+                                                   const float *prob, float thr, unsigned *prep,
+                                                   uint32_t *nbits_pre)
+{
+    __shared__ unsigned done;
+    const int n = *count;
+    const int c = threadIdx.x;
+    for (int b = blockIdx.x; b < n; b += gridDim.x) {
+        const int gid = list[b];
+        if (!(prob[b] > thr)) continue;  // the same for the whole CTA
+        if (c == 0) done = *(volatile unsigned *)&prep[gid];
+        __syncthreads();
+        const bool skip = done != 0u;
+        __syncthreads();
+        if (skip) continue;
+        nbits_pre[(size_t)gid * CELLS + c] = cell_bits(kp, gid, c);
+        __syncthreads();
+        if (c == 0) {
+            __threadfence();
+            *(volatile unsigned *)&prep[gid] = 1u;
+            atomicAdd(&kp.ctrl->prepared, 1ull);
+        }
+    }
+}
+
 const StorageOps &ops_of(const KParams &kp)
 {
     switch (kp.storage) {
@@ -88,6 +135,26 @@ cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, doubl
 cudaError_t launch_block_pops(const KParams &kp, int rd, int slot, float *out, cudaStream_t s)
 {
     return ops_of(kp).block_pops(kp, rd, slot, out, s);
+}
+
+cudaError_t launch_frontier(const KParams &kp, const int *nsnap, unsigned *mark, int *list, int *count,
+                            int sms, cudaStream_t s)
+{
+    k_frontier<<<sms * 4, 256, 0, s>>>(kp, nsnap, mark, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(const KParams &kp, int par, const int *nsnap, const int *list,
+                            const int *count, float *feat, int sms, cudaStream_t s)
+{
+    return ops_of(kp).features(kp, par, nsnap, list, count, feat, sms, s);
+}
+
+cudaError_t launch_prepare(const KParams &kp, const int *list, const int *count, const float *prob,
+                           float thr, unsigned *prep, uint32_t *nbits_pre, int sms, cudaStream_t s)
+{
+    k_prepare<<<sms * 2, CELLS, 0, s>>>(kp, list, count, prob, thr, prep, nbits_pre);
+    return cudaGetLastError();
 }
 
 int max_ctas_per_sm_stream_kernels(int storage)

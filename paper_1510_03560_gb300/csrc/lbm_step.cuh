@@ -953,6 +953,7 @@ __global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->n_active[par ^ 1] = n_old + ncand;
         ctrl->ncand[par ^ 1] = 0;
+        ctrl->created += (unsigned long long)ncand;
     }
     typename S::T *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
     float4 *mac = kp.mac + (size_t)par * kp.mac_stride;
@@ -980,7 +981,18 @@ __global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
             }
             kp.nbr[(size_t)slot * NBR_STRIDE + c] = s;
         }
-        const uint32_t bits = cell_bits(kp, gid, c);
+        // the cell's solid word: prepared ahead by the activation proposer
+        // (the same value, computed earlier on a side stream), or computed now
+        unsigned prepared = 0;
+        if (kp.prep) {
+            prepared = *(volatile const unsigned *)&kp.prep[gid];
+            __threadfence();
+        }
+        const uint32_t bits = prepared ? __ldcg(kp.nbits_pre + (size_t)gid * CELLS + c) : cell_bits(kp, gid, c);
+        if (c == 0) {
+            kp.act_step[gid] = step + 1;
+            if (prepared) atomicAdd(&ctrl->prepared_hits, 1ull);
+        }
         kp.nbits[(size_t)slot * CELLS + c] = bits;
         const bool live = !(bits & 1u);
         const unsigned fluid = __ballot_sync(FULL, live && !((bits >> HELD_BIT) & 1u));
@@ -1681,6 +1693,96 @@ __global__ void __launch_bounds__(CELLS) k_block_pops(KParams kp, int rdbuf, int
         for (int i = 0; i < Q; ++i) out[(a * Q + i) * CELLS + c] = f[a][i];
 }
 
+// Features of the listed frontier blocks (include/lbm.h, proposer): one CTA
+// per block; warps 0-5 take the faces -x, +x, -y, +y, -z, +z and pull the 64
+// cells of the meshed neighbour that touch the block (held and solid cells
+// left out), warp 6 the neighbour flags.  par: the read buffer.  Only slots
+// below *nsnap, a count of meshed blocks taken between two steps, are read:
+// their table rows are complete, while a slot handed out later may not be
+// yet (this kernel may run beside the step kernels).
+template <int NC, int ST>
+__global__ void __launch_bounds__(THREADS) k_features(KParams kp, int par, const int *nsnap,
+                                                      const int *list, const int *count, float *feat)
+{
+    using S = Store<ST>;
+    __shared__ float acc[6][4];  // per face: sum rho0, sum rho1, cells, flux
+    const typename S::T *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
+    const float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
+    const int n = *count;
+    const int nmesh = *nsnap;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = blockIdx.x; b < n; b += gridDim.x) {
+        const int gid = list[b];
+        float *out = feat + (size_t)b * LBM_MLP_IN;
+        if (warp < 6) {
+            const int axis = warp >> 1, sgn = (warp & 1) ? 1 : -1;  // neighbour at gid + sgn e_axis
+            const int k = 13 + sgn * (axis == 0 ? 1 : (axis == 1 ? 3 : 9));
+            const int nid = neighbour_of(kp, gid, k);
+            const int slot = nid >= 0 ? kp.slot_of[nid] : SOLIDBLK;
+            float r0 = 0.f, r1 = 0.f, cnt = 0.f, flux = 0.f;
+            if (slot >= 0 && slot < nmesh) {
+                const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
+                const int layer = sgn < 0 ? 7 : 0;  // the neighbour's cells touching the block
+#pragma unroll 1
+                for (int pass = 0; pass < 2; ++pass) {
+                    const int idx = pass * 32 + lane, u = idx & 7, v = idx >> 3;
+                    const int lx = axis == 0 ? layer : u, ly = axis == 1 ? layer : (axis == 0 ? u : v),
+                              lz = axis == 2 ? layer : v;
+                    const int c = lx | (ly << 3) | (lz << 6);
+                    const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+                    const bool use = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+                    float ref[2] = {0.f, 0.f};
+                    if (S::DEV && use) {
+                        const float4 m = __ldg(mac_prev + (size_t)slot * CELLS + c);
+                        ref[0] = m.x;
+                        ref[1] = m.y;
+                    }
+                    Moments m;
+                    pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, use, false, ref,
+                                 [&]<int I>(int a, float f) { m.template add<I>(a, f); });
+                    if (use) {
+                        r0 += m.rho[0];
+                        r1 += NC == 2 ? m.rho[1] : 0.f;
+                        cnt += 1.f;
+                        // into the block: along -sgn e_axis
+                        const float j = m.j[0][axis] + (NC == 2 ? m.j[1][axis] : 0.f);
+                        flux -= (float)sgn * j;
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                r0 += __shfl_xor_sync(FULL, r0, o);
+                r1 += __shfl_xor_sync(FULL, r1, o);
+                cnt += __shfl_xor_sync(FULL, cnt, o);
+                flux += __shfl_xor_sync(FULL, flux, o);
+            }
+            if (lane == 0) {
+                acc[warp][0] = r0;
+                acc[warp][1] = r1;
+                acc[warp][2] = cnt;
+                acc[warp][3] = flux;
+            }
+        } else if (warp == 6 && lane < 27 && lane != 13) {
+            const int nid = neighbour_of(kp, gid, lane);
+            out[8 + lane - (lane > 13 ? 1 : 0)] = (nid >= 0 && kp.slot_of[nid] >= 0) ? 1.f : 0.f;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float r0 = 0.f, r1 = 0.f, cnt = 0.f;
+            for (int f = 0; f < 6; ++f) {
+                r0 += acc[f][0];
+                r1 += acc[f][1];
+                cnt += acc[f][2];
+                out[2 + f] = acc[f][3];
+            }
+            out[0] = cnt > 0.f ? r0 / cnt : kp.rho_amb[0];
+            out[1] = cnt > 0.f ? r1 / cnt : kp.rho_amb[1];
+        }
+        __syncthreads();
+    }
+}
+
 // ---- launch wrappers of one storage form -------------------------------------
 
 // Resident CTAs per SM of a kernel, looked up once per process.
@@ -1787,6 +1889,15 @@ struct Launch {
         k_block_pops<ST><<<1, CELLS, 0, s>>>(kp, rd, slot, out);
         return cudaGetLastError();
     }
+    static cudaError_t features(const KParams &kp, int par, const int *nsnap, const int *list,
+                                const int *count, float *feat, int sms, cudaStream_t s)
+    {
+        if (kp.ncomp == 2)
+            k_features<2, ST><<<sms * 2, THREADS, 0, s>>>(kp, par, nsnap, list, count, feat);
+        else
+            k_features<1, ST><<<sms * 2, THREADS, 0, s>>>(kp, par, nsnap, list, count, feat);
+        return cudaGetLastError();
+    }
     // CTAs per SM that both streaming kernels can keep resident
     static int ctas_per_sm()
     {
@@ -1802,8 +1913,8 @@ struct Launch {
     }
     static const StorageOps *ops()
     {
-        static const StorageOps table = {init,   init_finish, ambient_slot, macro,      activate,
-                                         collide, output,     mass_partial, block_pops, ctas_per_sm};
+        static const StorageOps table = {init,    init_finish, ambient_slot, macro,      activate, collide,
+                                         output,  mass_partial, block_pops, features, ctas_per_sm};
         return &table;
     }
 };

@@ -54,14 +54,21 @@ class Stats(C.Structure):
         ("cell_updates", C.c_longlong), ("fluid_updates", C.c_longlong),
         ("launches", C.c_longlong), ("device_bytes", C.c_longlong),
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_longlong * 4),
+        ("created_blocks", C.c_longlong), ("prepared_blocks", C.c_longlong),
+        ("prepared_hits", C.c_longlong),
     ]
 
 
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_step", "lbm_step_async",
            "lbm_sync", "lbm_get_macro", "lbm_active_blocks", "lbm_mass",
            "lbm_get_block_populations", "lbm_velocities", "lbm_set_profiling", "lbm_get_stats",
-           "lbm_last_error", "lbm_mass_noalloc"]
+           "lbm_last_error", "lbm_mass_noalloc", "lbm_frontier_features", "lbm_activation_steps",
+           "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_set_params", "lbm_mlp_get_params",
+           "lbm_mlp_set_scaling", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
+           "lbm_set_proposer"]
 NOALLOC_MAX_BLOCKS = 65536
+MLP_IN, MLP_HIDDEN = 34, 64
+MLP_NPARAM = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
 
 _lib = None
 
@@ -98,6 +105,17 @@ def load():
     lib.lbm_last_error.argtypes = [vp]
     lib.lbm_last_error.restype = C.c_char_p
     lib.lbm_mass_noalloc.argtypes = [vp, vp, C.c_longlong, C.c_int, dp, vp]
+    lib.lbm_frontier_features.argtypes = [vp, ip, fp, C.c_longlong, C.POINTER(C.c_longlong)]
+    lib.lbm_activation_steps.argtypes = [vp, ip]
+    lib.lbm_mlp_create.argtypes = [C.c_int, vp, C.POINTER(vp)]
+    lib.lbm_mlp_destroy.argtypes = [vp]
+    lib.lbm_mlp_set_params.argtypes = [vp, fp]
+    lib.lbm_mlp_get_params.argtypes = [vp, fp]
+    lib.lbm_mlp_set_scaling.argtypes = [vp, fp, fp]
+    lib.lbm_mlp_forward.argtypes = [vp, vp, C.c_int, C.c_int, vp]
+    lib.lbm_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, dp, fp]
+    lib.lbm_mlp_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int]
+    lib.lbm_set_proposer.argtypes = [vp, vp, C.c_int, C.c_float]
     for name in EXPORTS:
         if name != "lbm_last_error":
             getattr(lib, name).restype = C.c_int
@@ -178,6 +196,7 @@ class LBM:
         p = Params()
         p.nx, p.ny, p.nz = int(kw["nx"]), int(kw["ny"]), int(kw["nz"])
         self.shape = (p.nz, p.ny, p.nx)
+        self.nblocks = (p.nx // EDGE) * (p.ny // EDGE) * (p.nz // EDGE)
         p.ncomp = int(kw.get("ncomp", 2))
         self.ncomp = p.ncomp
         per = kw.get("periodic", (1, 1, 0))
@@ -292,6 +311,107 @@ class LBM:
         d["kernel_ms"] = list(s.kernel_ms)
         d["kernel_launches"] = list(s.kernel_launches)
         return d
+
+
+def _lbm_frontier_features(self):
+    """Frontier blocks (ascending) and their LBM_MLP_IN features."""
+    n = C.c_longlong(0)
+    self._check(self.lib.lbm_frontier_features(self.h, None, None, 0, C.byref(n)))
+    cap = n.value
+    ids = np.zeros(max(cap, 1), dtype=np.int32)
+    feat = np.zeros((max(cap, 1), MLP_IN), dtype=np.float32)
+    self._check(self.lib.lbm_frontier_features(self.h, ids.ctypes.data_as(C.POINTER(C.c_int32)),
+                                               _fptr(feat), cap, C.byref(n)))
+    m = min(cap, n.value)
+    return ids[:m].copy(), feat[:m].copy()
+
+
+def _lbm_activation_steps(self):
+    """Per block: 0 initial, t + 1 when created in step t, -1 unmeshed."""
+    out = np.zeros(self.nblocks, dtype=np.int32)
+    self._check(self.lib.lbm_activation_steps(self.h, out.ctypes.data_as(C.POINTER(C.c_int32))))
+    return out
+
+
+def _lbm_set_proposer(self, mlp, period=16, threshold=0.5):
+    """Use an MLP (or None to turn the proposer off)."""
+    self._proposer = mlp
+    self._check(self.lib.lbm_set_proposer(self.h, None if mlp is None else mlp.h, int(period),
+                                          float(threshold)))
+
+
+LBM.frontier_features = _lbm_frontier_features
+LBM.activation_steps = _lbm_activation_steps
+LBM.set_proposer = _lbm_set_proposer
+
+
+class MLP:
+    """lbm_mlp: the activation proposer's network, trained and run by the
+    library's kernels.  Data arrays are torch CUDA tensors (float32)."""
+
+    def __init__(self, max_batch: int, stream=None):
+        import torch
+        self.lib = load()
+        self.torch_stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        rc = self.lib.lbm_mlp_create(int(max_batch), C.c_void_p(self.torch_stream.cuda_stream),
+                                     C.byref(h))
+        if rc != OK:
+            raise LBMError(rc, self.lib.lbm_last_error(None).decode())
+        self.h = h
+        self.max_batch = int(max_batch)
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LBMError(rc, self.lib.lbm_last_error(None).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lbm_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.shape == (MLP_NPARAM,)
+        self._check(self.lib.lbm_mlp_set_params(self.h, _fptr(p)))
+
+    def params(self) -> np.ndarray:
+        p = np.zeros(MLP_NPARAM, dtype=np.float32)
+        self._check(self.lib.lbm_mlp_get_params(self.h, _fptr(p)))
+        return p
+
+    def set_scaling(self, mean, scale):
+        m = np.ascontiguousarray(mean, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        assert m.shape == (MLP_IN,) and sc.shape == (MLP_IN,)
+        self._check(self.lib.lbm_mlp_set_scaling(self.h, _fptr(m), _fptr(sc)))
+
+    def forward(self, x, bf16: bool = False):
+        import torch
+        x = x.contiguous()
+        n = x.shape[0]
+        prob = torch.empty(n, dtype=torch.float32, device=x.device)
+        self._check(self.lib.lbm_mlp_forward(self.h, C.c_void_p(x.data_ptr()), n, 1 if bf16 else 0,
+                                             C.c_void_p(prob.data_ptr())))
+        return prob
+
+    def loss_grad(self, x, y, want_grad: bool = False):
+        x, y = x.contiguous(), y.contiguous()
+        loss = C.c_double(0.0)
+        g = np.zeros(MLP_NPARAM, dtype=np.float32) if want_grad else None
+        self._check(self.lib.lbm_mlp_loss_grad(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                               int(x.shape[0]), C.byref(loss),
+                                               _fptr(g) if g is not None else None))
+        return loss.value, g
+
+    def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.lib.lbm_mlp_adam(self.h, float(lr), float(beta1), float(beta2), float(eps), int(t)))
 
 
 def from_case(case, **over):
