@@ -138,11 +138,13 @@ def make_case(S=None, size=256):
     return W.porous_injection(**kw)
 
 
-def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32", proposer=None):
+def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32", proposer=None,
+              exec_mode="stream"):
     """Warm up, then time `steps` steps one by one (L2 flushed before each).
     proposer: an lbm MLP to run the activation proposer with (period 16,
     threshold 0.5)."""
     sim = L.from_case(case, progressive=progressive, storage=storage)
+    sim.set_exec(exec_mode)
     if proposer is not None:
         sim.set_proposer(proposer, period=16, threshold=0.5)
     sim.step(warmup)
@@ -284,6 +286,8 @@ def main():
                     help="time the static mesh only (profiling captures)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="population storage form (arithmetic is FP32 in all)")
+    ap.add_argument("--exec", default="stream", choices=["stream", "graph", "persistent"],
+                    help="how the library enqueues the steps")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip timing the FP16, BF16 and learned-proposer forms")
     args = ap.parse_args()
@@ -316,7 +320,8 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, args.storage)
+    prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, args.storage,
+                     exec_mode=args.exec)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -381,7 +386,7 @@ def main():
     config = {
         "workload": WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}",
         "mode": "progressive", "grid": [args.size] * 3, "block": [8, 8, 8],
-        "storage": args.storage,
+        "storage": args.storage, "exec": args.exec,
         "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
         "mean_active_fraction": round(prog["cells"] / 512 / args.steps / prog["total_blocks"], 4),

@@ -50,6 +50,15 @@ extern "C" {
 #define LBM_ENOMEM 2  /* block pool full, or a device allocation failed */
 #define LBM_ECUDA 3   /* a CUDA runtime call failed */
 #define LBM_ESTATE 4  /* call out of order (e.g. lbm_step before lbm_set_geometry) */
+#define LBM_ETIMEOUT 5 /* a bounded device wait gave up (grid barrier of LBM_EXEC_PERSISTENT) */
+
+/* How lbm_step enqueues the steps (lbm_set_exec); every mode runs the same
+ * per-cell code and gives the same results bit for bit. */
+#define LBM_EXEC_STREAM 0     /* three launches per step (default) */
+#define LBM_EXEC_GRAPH 1      /* the launches of two steps captured once as a CUDA graph,
+                                 replayed (the kernels read the step count on the device) */
+#define LBM_EXEC_PERSISTENT 2 /* the steps of a call in one cooperative launch, with grid
+                                 barriers between the phases (waits bounded: LBM_ETIMEOUT) */
 
 #define LBM_CELL_FLUID 0
 #define LBM_CELL_SOLID 1
@@ -240,6 +249,19 @@ const char *lbm_last_error(const lbm_ctx *ctx);
 int lbm_mass_noalloc(const float *f, const uint32_t *solid, long long nblocks, int ncomp,
                      double *mass, void *stream);
 
+
+/* Select LBM_EXEC_STREAM, _GRAPH or _PERSISTENT for later steps.  With
+ * the proposer on, launches are split at its rounds.  With profiling on,
+ * the device time of a graph or cooperative launch is counted as kind 3.
+ * Errors: LBM_EINVAL (unknown mode, or no cooperative launch on the
+ * device). */
+int lbm_set_exec(lbm_ctx *ctx, int mode);
+
+/* Test hook of the bounded device wait: one cooperative launch whose grid
+ * barrier expects `missing` more CTAs than it has, polling at most `spins`
+ * times; returns the resulting status (LBM_OK when missing is 0,
+ * LBM_ETIMEOUT otherwise) without affecting any context. */
+int lbm_barrier_selftest(int missing, long long spins);
 
 /* ---- learned activation proposer ------------------------------------------
  * Not part of the paper.  A small network predicts which unmeshed blocks the

@@ -87,6 +87,11 @@ struct lbm_ctx {
     float threshold = 0.5f;
     cudaStream_t side = nullptr;
     cudaEvent_t side_ev = nullptr;
+    // execution mode
+    int exec = LBM_EXEC_STREAM;
+    cudaStream_t cap = nullptr;        // capture stream of the step graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;   // two steps
 };
 
 namespace {
@@ -302,13 +307,69 @@ int enqueue_proposer(lbm_ctx *c, int t)
     return LBM_OK;
 }
 
+void drop_graph(lbm_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->gexec = nullptr;
+    c->graph = nullptr;
+}
+
+// The launches of one step on stream s.
+cudaError_t launch_step(lbm_ctx *c, cudaStream_t s)
+{
+    cudaError_t e = launch_macro(c->kp, 0, c->p.progressive ? 1 : 0, c->sms, s);
+    if (e == cudaSuccess && c->p.progressive) e = launch_activate(c->kp, 0, c->sms, s);
+    if (e == cudaSuccess) e = launch_collide(c->kp, 0, c->sms, s);
+    return e;
+}
+
+// Two steps captured as a graph (once; dropped when the parameters change).
+int ensure_graph(lbm_ctx *c)
+{
+    if (c->gexec) return LBM_OK;
+    if (!c->cap) CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CUDA_OR_FAIL(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_step(c, c->cap);
+    if (e == cudaSuccess) e = launch_step(c, c->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(c, LBM_ECUDA, "step graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    c->graph = g;
+    CUDA_OR_FAIL(c, cudaGraphInstantiate(&c->gexec, g, 0));
+    return LBM_OK;
+}
+
 int enqueue_steps(lbm_ctx *c, int nsteps)
 {
-    for (int k = 0; k < nsteps; ++k) {
+    int k = 0;
+    while (k < nsteps) {
         const int t = (int)(c->step + k);
         if (c->mlp && t % c->period == 0) {
             int rc = enqueue_proposer(c, t);
             if (rc) return rc;
+        }
+        // steps up to the next proposer round
+        int chunk = nsteps - k;
+        if (c->mlp) chunk = std::min(chunk, c->period - t % c->period);
+        if (c->exec == LBM_EXEC_PERSISTENT) {
+            CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] {
+                             return launch_run(c->kp, chunk, c->p.progressive ? 1 : 0, c->sms, c->stream);
+                         }));
+            k += chunk;
+            continue;
+        }
+        if (c->exec == LBM_EXEC_GRAPH && chunk >= 2) {
+            int rc = ensure_graph(c);
+            if (rc) return rc;
+            for (int p = 0; p < chunk / 2; ++p)
+                CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return cudaGraphLaunch(c->gexec, c->stream); }));
+            k += 2 * (chunk / 2);
+            continue;
         }
         CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
                          return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
@@ -317,6 +378,7 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
             CUDA_OR_FAIL(c, timed(c, K_ACTIVATE,
                                   [&] { return launch_activate(c->kp, t, c->sms, c->stream); }));
         CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, c->sms, c->stream); }));
+        k += 1;
     }
     c->step += nsteps;
     return LBM_OK;
@@ -342,6 +404,10 @@ int finish(lbm_ctx *c)
                         "block pool full at step %d: %d meshed + %d new blocks > capacity %d",
                         ctrl.fail_step, ctrl.n_active[ctrl.fail_step & 1],
                         ctrl.ncand[ctrl.fail_step & 1], c->capacity);
+        if (ctrl.status == LBM_ETIMEOUT) {
+            c->step = ctrl.step;
+            return fail(c, LBM_ETIMEOUT, "a grid barrier wait timed out after step %d", ctrl.step);
+        }
         return fail(c, ctrl.status, "device error %d at step %d", ctrl.status, ctrl.fail_step);
     }
     return LBM_OK;
@@ -391,6 +457,7 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     c->ctas_per_sm = max_ctas_per_sm_stream_kernels(p->storage);
     fill_physics(c);
+    c->kp.barrier_spins = 1ll << 24;  // about a second of polling
 
     const bool dev16 = p->storage != LBM_STORAGE_FP32;
     const size_t slot_floats = (size_t)(dev16 ? 1 : p->ncomp) * Q * CELLS;
@@ -462,6 +529,8 @@ int lbm_destroy(lbm_ctx *c)
     free_all(c);
     if (c->side_ev) cudaEventDestroy(c->side_ev);
     if (c->side) cudaStreamDestroy(c->side);
+    drop_graph(c);
+    if (c->cap) cudaStreamDestroy(c->cap);
     cudaStreamSynchronize(c->stream);
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     delete c;
@@ -477,6 +546,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     DeviceGuard g(c->device);
     if (!g.ok) return fail(c, LBM_ECUDA, "cannot select device %d", c->device);
     if (c->side) CUDA_OR_FAIL(c, cudaStreamSynchronize(c->side));
+    drop_graph(c);
     const lbm_params &p = c->p;
     const long long ncell = (long long)p.nx * p.ny * p.nz;
     const int nc = p.ncomp;
@@ -904,6 +974,7 @@ int lbm_set_proposer(lbm_ctx *c, lbm_mlp *mlp, int period, float threshold)
 {
     if (!c) return LBM_EINVAL;
     DeviceGuard g(c->device);
+    drop_graph(c);
     if (!mlp) {
         if (c->side) CUDA_OR_FAIL(c, cudaStreamSynchronize(c->side));
         c->mlp = nullptr;
@@ -926,6 +997,30 @@ int lbm_set_proposer(lbm_ctx *c, lbm_mlp *mlp, int period, float threshold)
     c->kp.prep = c->prep;
     c->kp.nbits_pre = c->nbits_pre;
     return LBM_OK;
+}
+
+int lbm_set_exec(lbm_ctx *c, int mode)
+{
+    if (!c) return LBM_EINVAL;
+    if (mode != LBM_EXEC_STREAM && mode != LBM_EXEC_GRAPH && mode != LBM_EXEC_PERSISTENT)
+        return fail(c, LBM_EINVAL, "unknown execution mode %d", mode);
+    DeviceGuard g(c->device);
+    if (mode == LBM_EXEC_PERSISTENT) {
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);
+        if (!coop) return fail(c, LBM_EINVAL, "the device has no cooperative launch");
+    }
+    c->exec = mode;
+    return LBM_OK;
+}
+
+int lbm_barrier_selftest(int missing, long long spins)
+{
+    if (missing < 0 || spins < 1) return LBM_EINVAL;
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ECUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return barrier_selftest(missing, spins, sms);
 }
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err : g_create_error; }

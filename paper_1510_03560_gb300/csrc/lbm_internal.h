@@ -34,6 +34,9 @@ struct Ctrl {
     unsigned long long created;        // blocks created by the criterion
     unsigned long long prepared;       // blocks prepared by the activation proposer
     unsigned long long prepared_hits;  // created blocks that had been prepared
+    int step;          // completed steps, advanced on the device by each step
+    unsigned collide_done;     // CTAs of the current collide launch that finished
+    unsigned bar_count, bar_gen;   // grid barrier of the multi-step kernel
     float psi_amb;     // psi of the ambient density, evaluated on the device
     int check_site;    // checked builds: first failed index check (site id)
     long long check_value;  // and the offending value
@@ -89,6 +92,7 @@ struct KParams {
     size_t buf_stride;  // elements (floats or words) per population buffer
     int slot_floats;    // elements per slot: ncomp * Q * CELLS (FP32) or
                         // Q * CELLS (16-bit forms)
+    long long barrier_spins;  // bounded wait of a grid barrier (polls)
 };
 
 // Kernel kinds for per-kernel timing.
@@ -108,6 +112,8 @@ struct StorageOps {
     cudaError_t (*features)(const KParams &, int, const int *, const int *, const int *, float *, int,
                             cudaStream_t);
     int (*ctas_per_sm)();
+    // nsteps whole steps in one cooperative launch
+    cudaError_t (*run)(const KParams &, int, int, int, cudaStream_t);
 };
 const StorageOps *storage_ops_fp32();
 const StorageOps *storage_ops_fp16();
@@ -133,6 +139,13 @@ cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, doubl
                         cudaStream_t s);
 // FP32 populations of one slot of buffer rd into out[ncomp][Q][CELLS] (16-bit forms).
 cudaError_t launch_block_pops(const KParams &kp, int rd, int slot, float *out, cudaStream_t s);
+// nsteps steps in one cooperative launch with grid barriers between the
+// phases (bounded waits: a barrier that does not complete sets
+// LBM_ETIMEOUT in the control words).
+cudaError_t launch_run(const KParams &kp, int nsteps, int progressive, int sms, cudaStream_t s);
+// One grid barrier that expects `missing` more CTAs than are launched, on
+// a scratch control block (tests of the bounded wait); returns the status.
+int barrier_selftest(int missing, long long spins, int sms);
 int max_ctas_per_sm_stream_kernels(int storage);
 
 // Frontier blocks and their features (lbm_kernels.cu; features per storage

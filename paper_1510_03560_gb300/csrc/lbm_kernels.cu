@@ -76,6 +76,13 @@ __global__ void __launch_bounds__(CELLS) k_prepare(KParams kp, const int *list, 
     }
 }
 
+// One grid barrier expecting `missing` more CTAs than launched (it can only
+// complete when missing is 0), for tests of the bounded wait.
+__global__ void __launch_bounds__(128) k_barrier_selftest(Ctrl *ctrl, int missing, long long spins)
+{
+    grid_sync(ctrl, gridDim.x + (unsigned)missing, spins);
+}
+
 const StorageOps &ops_of(const KParams &kp)
 {
     switch (kp.storage) {
@@ -155,6 +162,30 @@ cudaError_t launch_prepare(const KParams &kp, const int *list, const int *count,
 {
     k_prepare<<<sms * 2, CELLS, 0, s>>>(kp, list, count, prob, thr, prep, nbits_pre);
     return cudaGetLastError();
+}
+
+cudaError_t launch_run(const KParams &kp, int nsteps, int progressive, int sms, cudaStream_t s)
+{
+    return ops_of(kp).run(kp, nsteps, progressive, sms, s);
+}
+
+int barrier_selftest(int missing, long long spins, int sms)
+{
+    Ctrl *ctrl = nullptr;
+    if (cudaMalloc(&ctrl, sizeof(Ctrl)) != cudaSuccess) return LBM_ENOMEM;
+    cudaMemset(ctrl, 0, sizeof(Ctrl));
+    void *args[] = {&ctrl, &missing, &spins};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_barrier_selftest, sms, 128, args, 0, 0);
+    int status = LBM_ECUDA;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) {
+        Ctrl h{};
+        if (cudaMemcpy(&h, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost) == cudaSuccess) status = h.status;
+    } else {
+        cudaGetLastError();
+    }
+    cudaFree(ctrl);
+    return status;
 }
 
 int max_ctas_per_sm_stream_kernels(int storage)

@@ -70,6 +70,22 @@ __device__ __forceinline__ bool in_range(const KParams &kp, long long v, long lo
 #else
 __device__ __forceinline__ bool in_range(const KParams &, long long, long long, int) { return true; }
 #endif
+// End of a step's collide launch: the last CTA to finish advances the
+// device step counter (every CTA read it at its start), so that a captured
+// sequence of step launches can be replayed.
+__device__ __forceinline__ void step_done(Ctrl *ctrl, int step)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ctrl->collide_done, 1u) == gridDim.x - 1) {
+            ctrl->collide_done = 0u;
+            if (ctrl->status == 0) ctrl->step = step + 1;
+            __threadfence();
+        }
+    }
+}
+
 constexpr int THREADS = 256;            // threads per CTA of the cell kernels
 // resident CTAs per SM the deviation-form step kernels are compiled for
 // (fewer registers would spill)
@@ -780,7 +796,7 @@ __device__ __forceinline__ void criterion_mark(const KParams &kp, Ctrl *ctrl, in
 // Pass 1 of a step (FP32 form): streaming and moments over the meshed
 // blocks; with `criterion`, Eq. 13 at fluid cells bordering unmeshed blocks.
 template <int NC>
-__global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int criterion)
+__device__ __forceinline__ void macro_body(const KParams &kp, int step, int criterion)
 {
     constexpr int ST = LBM_STORAGE_FP32;
     Ctrl *ctrl = kp.ctrl;
@@ -817,6 +833,12 @@ __global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int step, int cri
                            make_float4(0.f, 0.f, 0.f, 0.f), rho, u);
         if (criterion) criterion_mark<NC>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
     }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int criterion)
+{
+    macro_body<NC>(kp, kp.ctrl->step, criterion);
 }
 
 // Per weight class: w rho_prev (the references of a cell's incoming values)
@@ -862,7 +884,7 @@ __device__ __forceinline__ void dev_item(const KParams &kp, const uint32_t *rd, 
 // Pass 1 of a step in the deviation forms (as k_macro).  Held cells keep
 // their density: mac of this step is a copy of the previous one.
 template <int NC, int ST>
-__global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KParams kp, int step, int criterion)
+__device__ __forceinline__ void macro_dev_body(const KParams &kp, int step, int criterion)
 {
     Ctrl *ctrl = kp.ctrl;
     if (criterion && ctrl->status) return;
@@ -919,6 +941,12 @@ __global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KPara
     }
 }
 
+template <int NC, int ST>
+__global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KParams kp, int criterion)
+{
+    macro_dev_body<NC, ST>(kp, kp.ctrl->step, criterion);
+}
+
 // Block creation (Sec. 4.2-4.3): the candidates found by k_macro get slots
 // after the meshed ones, start from the ambient resting equilibrium in both
 // buffers (R14) and get their streaming and moments of this step computed,
@@ -927,7 +955,7 @@ __global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KPara
 // non-solid cell of the other one), against the previous densities of the
 // reading cells, and give the block the ambient density as its previous one.
 template <int NC, int ST>
-__global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
+__device__ __forceinline__ void activate_body(const KParams &kp, int step)
 {
     using S = Store<ST>;
     Ctrl *ctrl = kp.ctrl;
@@ -1034,6 +1062,12 @@ __global__ void __launch_bounds__(THREADS) k_activate(KParams kp, int step)
     }
 }
 
+template <int NC, int ST>
+__global__ void __launch_bounds__(THREADS) k_activate(KParams kp)
+{
+    activate_body<NC, ST>(kp, kp.ctrl->step);
+}
+
 // Forces on a fluid cell (Eqs. 8-9 as read, gravity, adhesion), from the
 // mac values of its 18 neighbours.  A solid neighbour lends the centre's own
 // values; an unmeshed one the ambient values.  The mac copy in use starts
@@ -1112,7 +1146,7 @@ __device__ __forceinline__ void forces(const KParams &kp, const WarpNbr &wn, uin
 // velocity is kept for the next criterion at cells that border unmeshed
 // blocks.
 template <int NC, bool TAU1>
-__global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
+__device__ __forceinline__ void collide_body(const KParams &kp, int step)
 {
     constexpr int ST = LBM_STORAGE_FP32;
     Ctrl *ctrl = kp.ctrl;
@@ -1202,6 +1236,14 @@ __global__ void __launch_bounds__(THREADS) k_collide(KParams kp, int step)
     }
 }
 
+template <int NC, bool TAU1>
+__global__ void __launch_bounds__(THREADS) k_collide(KParams kp)
+{
+    const int step = *(volatile const int *)&kp.ctrl->step;
+    collide_body<NC, TAU1>(kp, step);
+    step_done(kp.ctrl, step);
+}
+
 // forces() for both components at once (same terms, paired arithmetic):
 // F[d] = (F_0, F_1) along axis d.  The mac copy in use starts at kp.mac +
 // moff.  All lanes must call; `live` masks the loads.
@@ -1282,7 +1324,7 @@ __device__ __forceinline__ float2 edot(const float2 *a, const float2 *na)
 
 // Pass 1 of a step, FP32 form with two components, paired arithmetic (as
 // k_macro).
-__global__ void __launch_bounds__(THREADS, 4) k_macro2(KParams kp, int step, int criterion)
+__device__ __forceinline__ void macro2_body(const KParams &kp, int step, int criterion)
 {
     Ctrl *ctrl = kp.ctrl;
     if (criterion && ctrl->status) return;
@@ -1325,10 +1367,15 @@ __global__ void __launch_bounds__(THREADS, 4) k_macro2(KParams kp, int step, int
     }
 }
 
+__global__ void __launch_bounds__(THREADS, 4) k_macro2(KParams kp, int criterion)
+{
+    macro2_body(kp, kp.ctrl->step, criterion);
+}
+
 // Pass 2 of a step, FP32 form with two components, paired arithmetic (as
 // k_collide).
 template <bool TAU1>
-__global__ void __launch_bounds__(THREADS) k_collide2(KParams kp, int step)
+__device__ __forceinline__ void collide2_body(const KParams &kp, int step)
 {
     Ctrl *ctrl = kp.ctrl;
     if (ctrl->status) return;
@@ -1421,6 +1468,14 @@ __global__ void __launch_bounds__(THREADS) k_collide2(KParams kp, int step)
     }
 }
 
+template <bool TAU1>
+__global__ void __launch_bounds__(THREADS) k_collide2(KParams kp)
+{
+    const int step = *(volatile const int *)&kp.ctrl->step;
+    collide2_body<TAU1>(kp, step);
+    step_done(kp.ctrl, step);
+}
+
 // Pass 2 of a step in the deviation forms (as k_collide, paired arithmetic
 // for the two components).  Every value
 // is stored against the density its reader has now: the neighbour's mac of
@@ -1429,7 +1484,7 @@ __global__ void __launch_bounds__(THREADS) k_collide2(KParams kp, int step)
 // mac, velocity from uprev).  With one component the second half of each
 // word carries a dummy unit-density state.
 template <int NC, bool TAU1, int ST>
-__global__ void __launch_bounds__(THREADS, DEV_COLLIDE_MIN_CTAS) k_collide_dev(KParams kp, int step)
+__device__ __forceinline__ void collide_dev_body(const KParams &kp, int step)
 {
     using S = Store<ST>;
     Ctrl *ctrl = kp.ctrl;
@@ -1547,6 +1602,14 @@ __global__ void __launch_bounds__(THREADS, DEV_COLLIDE_MIN_CTAS) k_collide_dev(K
             }
         }
     }
+}
+
+template <int NC, bool TAU1, int ST>
+__global__ void __launch_bounds__(THREADS, DEV_COLLIDE_MIN_CTAS) k_collide_dev(KParams kp)
+{
+    const int step = *(volatile const int *)&kp.ctrl->step;
+    collide_dev_body<NC, TAU1, ST>(kp, step);
+    step_done(kp.ctrl, step);
 }
 
 // Macroscopic output of one component for slots [slot0, slot0 + nslots):
@@ -1783,6 +1846,86 @@ __global__ void __launch_bounds__(THREADS) k_features(KParams kp, int par, const
     }
 }
 
+// ---- whole steps in one cooperative launch ----------------------------------
+
+// Grid-wide barrier with a bounded wait: CTA leaders count in; the last one
+// resets the count and advances the generation, the others poll it.  A
+// wait that exceeds `spins` polls sets LBM_ETIMEOUT and gives up, so no
+// launch can hang.  Returns false when the status is no longer 0.
+__device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned expect, long long spins)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &ctrl->bar_gen;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(&ctrl->bar_count, 1u) == expect - 1) {
+            ctrl->bar_count = 0u;
+            __threadfence();
+            atomicAdd(&ctrl->bar_gen, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g) {
+                if (++it > spins) {
+                    atomicCAS(&ctrl->status, 0, LBM_ETIMEOUT);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)&ctrl->status == 0;
+}
+
+// The phases of one storage form and component count.
+template <int NC, bool TAU1, int ST>
+struct Phases {
+    static constexpr int MIN_CTAS = Store<ST>::DEV ? DEV_COLLIDE_MIN_CTAS : 3;
+    __device__ __forceinline__ static void macro(const KParams &kp, int step, int crit)
+    {
+        if constexpr (Store<ST>::DEV)
+            macro_dev_body<NC, ST>(kp, step, crit);
+        else if constexpr (NC == 2)
+            macro2_body(kp, step, crit);
+        else
+            macro_body<NC>(kp, step, crit);
+    }
+    __device__ __forceinline__ static void collide(const KParams &kp, int step)
+    {
+        if constexpr (Store<ST>::DEV)
+            collide_dev_body<NC, TAU1, ST>(kp, step);
+        else if constexpr (NC == 2)
+            collide2_body<TAU1>(kp, step);
+        else
+            collide_body<NC, TAU1>(kp, step);
+    }
+};
+
+// nsteps steps: stream + moments (+ criterion), grid barrier, block
+// creation, barrier, forces + collision, barrier; the same bodies as the
+// per-phase launches, so the results are the same bit for bit.
+template <int NC, bool TAU1, int ST>
+__global__ void __launch_bounds__(THREADS, (Phases<NC, TAU1, ST>::MIN_CTAS)) k_run(KParams kp, int nsteps,
+                                                                              int progressive)
+{
+    using P = Phases<NC, TAU1, ST>;
+    Ctrl *ctrl = kp.ctrl;
+    int step = *(volatile int *)&ctrl->step;
+    for (int k = 0; k < nsteps; ++k, ++step) {
+        P::macro(kp, step, progressive);
+        if (!grid_sync(ctrl, gridDim.x, kp.barrier_spins)) return;
+        if (progressive) {
+            activate_body<NC, ST>(kp, step);
+            if (!grid_sync(ctrl, gridDim.x, kp.barrier_spins)) return;
+        }
+        P::collide(kp, step);
+        if (!grid_sync(ctrl, gridDim.x, kp.barrier_spins)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->step = step + 1;
+    }
+}
+
 // ---- launch wrappers of one storage form -------------------------------------
 
 // Resident CTAs per SM of a kernel, looked up once per process.
@@ -1835,19 +1978,19 @@ struct Launch {
     static cudaError_t macro(const KParams &kp, int step, int criterion, int sms, cudaStream_t s)
     {
         if constexpr (Store<ST>::DEV) {
-            if (kp.ncomp == 2) return launch_persistent<k_macro_dev<2, ST>>(sms, s, kp, step, criterion);
-            return launch_persistent<k_macro_dev<1, ST>>(sms, s, kp, step, criterion);
+            if (kp.ncomp == 2) return launch_persistent<k_macro_dev<2, ST>>(sms, s, kp, criterion);
+            return launch_persistent<k_macro_dev<1, ST>>(sms, s, kp, criterion);
         } else {
-            if (kp.ncomp == 2) return launch_persistent<k_macro2>(sms, s, kp, step, criterion);
-            return launch_persistent<k_macro<1>>(sms, s, kp, step, criterion);
+            if (kp.ncomp == 2) return launch_persistent<k_macro2>(sms, s, kp, criterion);
+            return launch_persistent<k_macro<1>>(sms, s, kp, criterion);
         }
     }
     static cudaError_t activate(const KParams &kp, int step, int sms, cudaStream_t s)
     {
         if (kp.ncomp == 2)
-            k_activate<2, ST><<<sms, THREADS, 0, s>>>(kp, step);
+            k_activate<2, ST><<<sms, THREADS, 0, s>>>(kp);
         else
-            k_activate<1, ST><<<sms, THREADS, 0, s>>>(kp, step);
+            k_activate<1, ST><<<sms, THREADS, 0, s>>>(kp);
         return cudaGetLastError();
     }
     static cudaError_t collide(const KParams &kp, int step, int sms, cudaStream_t s)
@@ -1855,18 +1998,18 @@ struct Launch {
         const bool tau1 = kp.omega == 1.0f;
         if constexpr (Store<ST>::DEV) {
             if (kp.ncomp == 2) {
-                if (tau1) return launch_persistent<k_collide_dev<2, true, ST>>(sms, s, kp, step);
-                return launch_persistent<k_collide_dev<2, false, ST>>(sms, s, kp, step);
+                if (tau1) return launch_persistent<k_collide_dev<2, true, ST>>(sms, s, kp);
+                return launch_persistent<k_collide_dev<2, false, ST>>(sms, s, kp);
             }
-            if (tau1) return launch_persistent<k_collide_dev<1, true, ST>>(sms, s, kp, step);
-            return launch_persistent<k_collide_dev<1, false, ST>>(sms, s, kp, step);
+            if (tau1) return launch_persistent<k_collide_dev<1, true, ST>>(sms, s, kp);
+            return launch_persistent<k_collide_dev<1, false, ST>>(sms, s, kp);
         } else {
             if (kp.ncomp == 2) {
-                if (tau1) return launch_persistent<k_collide2<true>>(sms, s, kp, step);
-                return launch_persistent<k_collide2<false>>(sms, s, kp, step);
+                if (tau1) return launch_persistent<k_collide2<true>>(sms, s, kp);
+                return launch_persistent<k_collide2<false>>(sms, s, kp);
             }
-            if (tau1) return launch_persistent<k_collide<1, true>>(sms, s, kp, step);
-            return launch_persistent<k_collide<1, false>>(sms, s, kp, step);
+            if (tau1) return launch_persistent<k_collide<1, true>>(sms, s, kp);
+            return launch_persistent<k_collide<1, false>>(sms, s, kp);
         }
     }
     static cudaError_t output(const KParams &kp, int rd, int comp, int slot0, int nslots, float *out,
@@ -1898,6 +2041,25 @@ struct Launch {
             k_features<1, ST><<<sms * 2, THREADS, 0, s>>>(kp, par, nsnap, list, count, feat);
         return cudaGetLastError();
     }
+    template <int NC, bool TAU1>
+    static cudaError_t run_on(const KParams &kp, int nsteps, int progressive, int sms, cudaStream_t s)
+    {
+        auto kern = k_run<NC, TAU1, ST>;
+        const int grid = sms * occupancy<k_run<NC, TAU1, ST>>();
+        KParams a = kp;
+        void *args[] = {&a, &nsteps, &progressive};
+        return cudaLaunchCooperativeKernel((const void *)kern, grid, THREADS, args, 0, s);
+    }
+    static cudaError_t run(const KParams &kp, int nsteps, int progressive, int sms, cudaStream_t s)
+    {
+        if (nsteps <= 0) return cudaSuccess;
+        const bool tau1 = kp.omega == 1.0f;
+        if (kp.ncomp == 2)
+            return tau1 ? run_on<2, true>(kp, nsteps, progressive, sms, s)
+                        : run_on<2, false>(kp, nsteps, progressive, sms, s);
+        return tau1 ? run_on<1, true>(kp, nsteps, progressive, sms, s)
+                    : run_on<1, false>(kp, nsteps, progressive, sms, s);
+    }
     // CTAs per SM that both streaming kernels can keep resident
     static int ctas_per_sm()
     {
@@ -1913,8 +2075,8 @@ struct Launch {
     }
     static const StorageOps *ops()
     {
-        static const StorageOps table = {init,    init_finish, ambient_slot, macro,      activate, collide,
-                                         output,  mass_partial, block_pops, features, ctas_per_sm};
+        static const StorageOps table = {init,    init_finish,  ambient_slot, macro,    activate,    collide,
+                                         output,  mass_partial, block_pops,   features, ctas_per_sm, run};
         return &table;
     }
 };

@@ -17,7 +17,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liblbm_checked.so" if os.environ.get("LBM_CHECKED") == "1"
                         else "liblbm.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ESTATE = 0, 1, 2, 3, 4
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, 1, 2, 3, 4, 5
+EXEC = {"stream": 0, "graph": 1, "persistent": 2}  # LBM_EXEC_*
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}  # LBM_STORAGE_*
 Q = 19
 EDGE = 8
@@ -65,7 +66,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_step", "lbm_ste
            "lbm_last_error", "lbm_mass_noalloc", "lbm_frontier_features", "lbm_activation_steps",
            "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_set_params", "lbm_mlp_get_params",
            "lbm_mlp_set_scaling", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
-           "lbm_set_proposer"]
+           "lbm_set_proposer", "lbm_set_exec", "lbm_barrier_selftest"]
 NOALLOC_MAX_BLOCKS = 65536
 MLP_IN, MLP_HIDDEN = 34, 64
 MLP_NPARAM = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
@@ -116,6 +117,8 @@ def load():
     lib.lbm_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, dp, fp]
     lib.lbm_mlp_adam.argtypes = [vp, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int]
     lib.lbm_set_proposer.argtypes = [vp, vp, C.c_int, C.c_float]
+    lib.lbm_set_exec.argtypes = [vp, C.c_int]
+    lib.lbm_barrier_selftest.argtypes = [C.c_int, C.c_longlong]
     for name in EXPORTS:
         if name != "lbm_last_error":
             getattr(lib, name).restype = C.c_int
@@ -340,6 +343,17 @@ def _lbm_set_proposer(self, mlp, period=16, threshold=0.5):
                                           float(threshold)))
 
 
+def _lbm_set_exec(self, mode):
+    """"stream", "graph" or "persistent" (or the LBM_EXEC_* code)."""
+    self._check(self.lib.lbm_set_exec(self.h, EXEC[mode] if isinstance(mode, str) else int(mode)))
+
+
+def barrier_selftest(missing: int, spins: int) -> int:
+    """Status of one bounded grid barrier that expects `missing` extra CTAs."""
+    return load().lbm_barrier_selftest(int(missing), int(spins))
+
+
+LBM.set_exec = _lbm_set_exec
 LBM.frontier_features = _lbm_frontier_features
 LBM.activation_steps = _lbm_activation_steps
 LBM.set_proposer = _lbm_set_proposer
