@@ -148,6 +148,40 @@ def porous_injection(n=(256, 256, 256), seed=1510035601, solid_frac=0.30, r_rang
                  block=block, g_ads=(g_ads, 0.0), grav=(0.0, 0.0, 0.0), S=S, **PHYSICS)
 
 
+def droplet_impact(n=(64, 64, 64), seed=1510035700, u_drop=0.03, g_ads=-0.2, S=3e-4,
+                   progressive=1, block=(8, 8, 8)):
+    """A liquid drop moving towards a wetting floor in a closed gas box.
+
+    Walls on every face; a sphere of radius max(4, min(n) / 6) centred
+    near the top (seeded jitter of the centre) holds component 0 at RHO_LIQ
+    and component 1 at 0.1, both moving at u_drop along -z; gas elsewhere
+    (component 0 at RHO_VAP, component 1 at 1.0).  Physics, ambient and S
+    as porous_injection, so that the two kinds of case can share one batch.
+    """
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    ct = np.zeros((nz, ny, nx), dtype=np.uint8)
+    ct[:, :, 0] = ct[:, :, nx - 1] = SOLID
+    ct[:, 0, :] = ct[:, ny - 1, :] = SOLID
+    ct[0, :, :] = ct[nz - 1, :, :] = SOLID
+    R = max(4.0, min(n) / 6.0)
+    c = (nx / 2 + rng.uniform(-0.1, 0.1) * nx, ny / 2 + rng.uniform(-0.1, 0.1) * ny,
+         nz - 2.0 * R - 2.0 + rng.uniform(-1.0, 1.0))
+    z, y, x = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    inside = ((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 < R * R) & (ct == FLUID)
+    rho = np.empty((2, nz, ny, nx), dtype=np.float32)
+    rho[0] = f32(RHO_VAP)
+    rho[1] = 1.0
+    rho[0][inside] = f32(RHO_LIQ)
+    rho[1][inside] = f32(0.1)
+    u = np.zeros((2, 3, nz, ny, nx), dtype=np.float32)
+    u[0, 2][inside] = f32(-u_drop)
+    u[1, 2][inside] = f32(-u_drop)
+    amb = (f32(RHO_VAP), 1.0)
+    return _case(ct, rho, u, amb, ncomp=2, periodic=(0, 0, 0), progressive=progressive,
+                 block=block, g_ads=(g_ads, 0.0), grav=(0.0, 0.0, 0.0), S=S, **PHYSICS)
+
+
 def droplet(n=32, R=8.0, center=None, progressive=0, block=(8, 8, 8), rho_vap=RHO_VAP):
     """Single-component Peng-Robinson droplet of radius R in vapour of
     density rho_vap, fully periodic box (Laplace test)."""
