@@ -93,6 +93,17 @@ constexpr int DEV_MACRO_MIN_CTAS = 3;
 constexpr int DEV_COLLIDE_MIN_CTAS = 2;
 constexpr int PARTS = CELLS / THREADS;  // CTA work items per block
 
+// Stores of a warp cover four 8-cell x-rows, one 32-byte sector per row
+// and population.  Every lane of the warp must call (a ballot).  A sector written only in part makes the memory read it
+// back to merge (read-modify-write under ECC), so a solid cell writes a
+// zero wherever another cell of its row writes: complete sectors.  Rows
+// with no writer stay untouched.  Solid cells' values are never read.
+__device__ __forceinline__ bool row_has(bool p)
+{
+    const unsigned m = __ballot_sync(0xffffffffu, p);
+    return (m >> ((threadIdx.x & 31) & 24u)) & 0xffu;
+}
+
 // ---- D3Q19 in this library's order: the 9 velocities with e_z = 0, then
 // the 5 with e_z = +1, then the 5 with e_z = -1; opposites are adjacent
 // within the first group and 5 apart across the other two. -------------
@@ -1177,6 +1188,9 @@ __device__ __forceinline__ void collide_body(const KParams &kp, int step)
             next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
         const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+        // every lane takes part in the ballot (it must not sit behind &&)
+        const bool row_live = row_has(live);
+        const bool fill = (bits & 1u) && row_live;  // solid cell completing a sector
         if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) continue;
         Moments m;
         float fin[TAU1 ? 1 : NC][Q];
@@ -1196,7 +1210,7 @@ __device__ __forceinline__ void collide_body(const KParams &kp, int step)
         }
         float F[2][3];
         forces<NC>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
-        if (!live) continue;
+        if (!live && !fill) continue;
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
             const float inv = 1.f / rho[a];
@@ -1220,11 +1234,11 @@ __device__ __forceinline__ void collide_body(const KParams &kp, int step)
                     v += (1.f - kp.omega) * (fin[a][I] - e0);
                 }
                 moving += v;
-                dst[I * CELLS] = v;
+                dst[I * CELLS] = live ? v : 0.f;
             });
-            dst[0] = r - moving;
+            dst[0] = live ? r - moving : 0.f;
         }
-        if (kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+        if (live && kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
 #pragma unroll
             for (int a = 0; a < NC; ++a) {
                 float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
@@ -1362,7 +1376,9 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
             u[0][d] = ud.x;
             u[1][d] = ud.y;
         }
-        if (live) kp.mac[(size_t)slot * CELLS + c] = mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y);
+        // solid cells write zeros too (never read): complete sectors
+        kp.mac[(size_t)slot * CELLS + c] =
+            live ? mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
         if (criterion) criterion_mark<2>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
     }
 }
@@ -1405,6 +1421,9 @@ __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
             next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
         const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+        // every lane takes part in the ballot (it must not sit behind &&)
+        const bool row_live = row_has(live);
+        const bool fill = (bits & 1u) && row_live;  // solid cell completing a sector
         if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) continue;
         Moments2 m;
         float2 fin[TAU1 ? 1 : Q];
@@ -1419,7 +1438,7 @@ __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
         for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
         float2 F[3];
         forces2<2>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
-        if (!live) continue;
+        if (!live && !fill) continue;
         float2 v[3], nv[3], nu[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1450,14 +1469,14 @@ __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
                 f = fma2(relax, sub2(fin[I], e0), f);
             }
             moving = add2(moving, f);
-            d0[I * CELLS] = f.x;
-            d1[I * CELLS] = f.y;
+            d0[I * CELLS] = live ? f.x : 0.f;
+            d1[I * CELLS] = live ? f.y : 0.f;
         });
         const float2 rest = sub2(rho, moving);
-        d0[0] = rest.x;
-        d1[0] = rest.y;
+        d0[0] = live ? rest.x : 0.f;
+        d1[0] = live ? rest.y : 0.f;
         (void)cu;
-        if (kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+        if (live && kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
             float *up = kp.uprev + (size_t)slot * 2 * 3 * CELLS + c;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
