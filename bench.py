@@ -130,10 +130,26 @@ def device_uuid(torch, dev):
         return None
 
 
-def make_case(S=None, size=256):
+# the other injection workloads: the same recipe on a larger grid (the
+# 16-bit storage forms are quoted on it) and a longer porous channel (the
+# learned form is quoted on it)
+WORKLOADS = {
+    "injection384": ("porous injection 384^3 (seed 1510035602, spheres r 6-12, solid 0.30, "
+                     "96^2 inlet u=0.02, g_ads=-0.2, 2 components), 8^3 blocks",
+                     dict(n=(384, 384, 384), seed=1510035602, inlet=96, x_free=24)),
+    "channel512": ("porous channel 512x256x256 (seed 1510035604, spheres r 6-12, solid 0.35, "
+                   "64^2 inlet u=0.03, g_ads=-0.2, 2 components), 8^3 blocks",
+                   dict(n=(512, 256, 256), seed=1510035604, solid_frac=0.35, inlet=64, u_in=0.03,
+                        x_free=16)),
+}
+
+
+def make_case(S=None, size=256, workload="injection"):
     from paper_1510_03560_gb300 import workloads as W
     kw = {} if S is None else {"S": S}
-    if size != 256:
+    if workload in WORKLOADS:
+        kw.update(WORKLOADS[workload][1])
+    elif size != 256:
         kw.update(n=(size, size, size), inlet=size // 4, x_free=max(size // 16, 4))
     return W.porous_injection(**kw)
 
@@ -353,8 +369,11 @@ def main():
                     help="time the static mesh only (profiling captures)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="population storage form (arithmetic is FP32 in all)")
-    ap.add_argument("--workload", default="injection", choices=["injection", "batch"],
-                    help="injection: the 256^3 headline; batch: 64 small simulations in one pool")
+    ap.add_argument("--workload", default="injection",
+                    choices=["injection", "batch", "injection384", "channel512"],
+                    help="injection: the 256^3 headline; batch: 64 small simulations in one pool; "
+                         "injection384 / channel512: the grids the 16-bit and learned forms are "
+                         "quoted on")
     ap.add_argument("--exec", default="stream", choices=["stream", "graph", "persistent"],
                     help="how the library enqueues the steps")
     ap.add_argument("--no-forms", action="store_true",
@@ -378,7 +397,7 @@ def main():
         dist.barrier()
     from paper_1510_03560_gb300 import lbm as L
     uuid = device_uuid(torch, local)
-    case = make_case(args.S, args.size)
+    case = make_case(args.S, args.size, args.workload)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if args.static_only:
         st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage)
@@ -455,8 +474,9 @@ def main():
     share = {name: round(v / max(sum(prog["kernel_ms"]), 1e-9), 4)
              for name, v in zip(("macro", "activate", "collide", "other"), prog["kernel_ms"])}
     config = {
-        "workload": WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}",
-        "mode": "progressive", "grid": [args.size] * 3, "block": [8, 8, 8],
+        "workload": (WORKLOADS[args.workload][0] if args.workload in WORKLOADS
+                     else WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}"),
+        "mode": "progressive", "grid": [case["params"][k] for k in ("nx", "ny", "nz")], "block": [8, 8, 8],
         "storage": args.storage, "exec": args.exec,
         "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
