@@ -294,7 +294,7 @@ def run_batch(args):
 
     modes = {}
     with ClockSampler(uuid) as clk:
-        for m in ("stream", "graph", "persistent"):
+        for m in ("stream", "graph", "persistent", "staged"):
             ms, cells, launches = timed(batch, m, args.steps, args.warmup)
             modes[m] = {"mlups": round(cells / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms / args.steps, 5),
                         "launches": launches}
@@ -374,7 +374,7 @@ def main():
                     help="injection: the 256^3 headline; batch: 64 small simulations in one pool; "
                          "injection384 / channel512: the grids the 16-bit and learned forms are "
                          "quoted on")
-    ap.add_argument("--exec", default="stream", choices=["stream", "graph", "persistent"],
+    ap.add_argument("--exec", default="stream", choices=["stream", "graph", "persistent", "staged"],
                     help="how the library enqueues the steps")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip timing the FP16, BF16 and learned-proposer forms")
@@ -400,7 +400,8 @@ def main():
     case = make_case(args.S, args.size, args.workload)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if args.static_only:
-        st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage)
+        st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage,
+                       exec_mode=args.exec)
         if rank == 0:
             print(json.dumps({"static_mlups": st["cells"] / (st["ms"] * 1e-3) / 1e6,
                               "ms": st["ms"], "kernel_ms": st["kernel_ms"],

@@ -59,6 +59,9 @@ extern "C" {
                                  replayed (the kernels read the step count on the device) */
 #define LBM_EXEC_PERSISTENT 2 /* the steps of a call in one cooperative launch, with grid
                                  barriers between the phases (waits bounded: LBM_ETIMEOUT) */
+#define LBM_EXEC_STAGED 3     /* as STREAM, with each block's populations brought into shared
+                                 memory by one bulk (TMA) copy, double buffered (FP32 with
+                                 two components; other forms run as STREAM) */
 
 #define LBM_CELL_FLUID 0
 #define LBM_CELL_SOLID 1

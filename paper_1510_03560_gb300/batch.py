@@ -128,7 +128,7 @@ def block_map(batch_params, placements, k):
     return (x0 // EDGE + bx) + NBX * ((y0 // EDGE + by) + NBY * (z0 // EDGE + bz))
 
 
-def autotune(L, case, steps: int = 40, modes=("stream", "graph", "persistent"), storage="fp32"):
+def autotune(L, case, steps: int = 40, modes=("stream", "graph", "persistent", "staged"), storage="fp32"):
     """Time `steps` steps in each execution mode on a scratch context (CUDA
     events on the library's stream) and return (best mode, {mode: ms})."""
     import torch

@@ -1002,7 +1002,8 @@ int lbm_set_proposer(lbm_ctx *c, lbm_mlp *mlp, int period, float threshold)
 int lbm_set_exec(lbm_ctx *c, int mode)
 {
     if (!c) return LBM_EINVAL;
-    if (mode != LBM_EXEC_STREAM && mode != LBM_EXEC_GRAPH && mode != LBM_EXEC_PERSISTENT)
+    if (mode != LBM_EXEC_STREAM && mode != LBM_EXEC_GRAPH && mode != LBM_EXEC_PERSISTENT &&
+        mode != LBM_EXEC_STAGED)
         return fail(c, LBM_EINVAL, "unknown execution mode %d", mode);
     DeviceGuard g(c->device);
     if (mode == LBM_EXEC_PERSISTENT) {
@@ -1011,6 +1012,8 @@ int lbm_set_exec(lbm_ctx *c, int mode)
         if (!coop) return fail(c, LBM_EINVAL, "the device has no cooperative launch");
     }
     c->exec = mode;
+    c->kp.staged = mode == LBM_EXEC_STAGED ? 1 : 0;
+    drop_graph(c);
     return LBM_OK;
 }
 

@@ -92,7 +92,8 @@ struct KParams {
     size_t buf_stride;  // elements (floats or words) per population buffer
     int slot_floats;    // elements per slot: ncomp * Q * CELLS (FP32) or
                         // Q * CELLS (16-bit forms)
-    long long barrier_spins;  // bounded wait of a grid barrier (polls)
+    long long barrier_spins;  // bounded wait of a grid barrier or a bulk copy (polls)
+    int staged;         // FP32, two components: TMA-staged pass kernels
 };
 
 // Kernel kinds for per-kernel timing.

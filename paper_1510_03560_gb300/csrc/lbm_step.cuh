@@ -1495,6 +1495,260 @@ __global__ void __launch_bounds__(THREADS) k_collide2(KParams kp)
     step_done(kp.ctrl, step);
 }
 
+// ---- TMA-staged step kernels (FP32, two components) -------------------------
+// One CTA of 512 threads per SM works on one block at a time: the block's
+// populations (both components, 77.8 KB, contiguous in the read buffer)
+// arrive in shared memory with one bulk copy (cp.async.bulk), double
+// buffered, so that the next block's copy is in flight while the current
+// one is processed.  Pulls from inside the block read shared memory; only
+// cells pulling across a face read the neighbour block in global memory.
+// Same arithmetic in the same order as k_macro2 / k_collide2.
+constexpr int TMA_THREADS = CELLS;
+constexpr uint32_t SLOT2_BYTES = 2u * Q * CELLS * 4u;
+constexpr size_t TMA_SMEM = 2 * (size_t)SLOT2_BYTES + 64;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// bytes: a multiple of 16; both addresses 16-byte aligned
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for a phase of an mbarrier
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long spins)
+{
+    for (long long i = 0; i < spins; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// The block loop: cell(slot, c, stage) for every meshed slot, c the thread's
+// cell, stage its block's populations ([comp][dir][cell] floats).  Only
+// thread 0 issues copies and waits (a bounded wait: on time-out the status
+// becomes LBM_ETIMEOUT, thread 0 waits again for its copies in flight, and
+// the whole CTA returns together).
+template <class Cell>
+__device__ __forceinline__ void staged_blocks(const KParams &kp, const float *rd, int n, Cell &&cell)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int arrived;
+    float *stage0 = reinterpret_cast<float *>(smem_raw);
+    float *stage1 = reinterpret_cast<float *>(smem_raw + SLOT2_BYTES);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + 2 * (size_t)SLOT2_BYTES);
+    const int G = gridDim.x;
+    int b = blockIdx.x;
+    if (b >= n) return;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) bulk_load(stage0, rd + (size_t)b * kp.slot_floats, SLOT2_BYTES, &bar[0]);
+    for (int k = 0; b < n; ++k, b += G) {
+        const int s = k & 1;
+        const int bn = b + G;
+        if (threadIdx.x == 0) {
+            if (bn < n) {
+                fence_proxy_async();
+                bulk_load(s ? stage0 : stage1, rd + (size_t)bn * kp.slot_floats, SLOT2_BYTES, &bar[s ^ 1]);
+            }
+            arrived = mbar_wait(&bar[s], (unsigned)(k >> 1) & 1u, kp.barrier_spins) ? 1 : 0;
+            if (!arrived) {
+                atomicCAS(&kp.ctrl->status, 0, LBM_ETIMEOUT);
+                mbar_wait(&bar[s], (unsigned)(k >> 1) & 1u, kp.barrier_spins);
+                if (bn < n) mbar_wait(&bar[s ^ 1], (unsigned)((k + 1) >> 1) & 1u, kp.barrier_spins);
+            }
+        }
+        __syncthreads();
+        if (!arrived) return;
+        cell(b, (int)threadIdx.x, s ? stage1 : stage0);
+        __syncthreads();  // the stage is free for the copy issued next iteration
+    }
+}
+
+// pull2_f32 with the block's own populations in shared memory (st).
+template <class Sink>
+__device__ __forceinline__ void pull2_staged(const WarpNbr &wn, const float *rd, const float *st, int c,
+                                             uint32_t bits, bool live, Sink &&sink)
+{
+    const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+    const bool held = (bits >> HELD_BIT) & 1u;
+    uint32_t off[Q];
+    uint32_t inside = 0;  // bit I: population I comes from the stage
+    Unroll<0, Q>::run([&]<int I>() {
+        const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+        const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+        const uint32_t base = __shfl_sync(FULL, wn.fbase, k);
+        const bool bounce = (bits >> I) & 1u;
+        const bool in = held || bounce || k == 13;
+        off[I] = held ? (uint32_t)(I * CELLS + c)
+                      : (bounce ? (uint32_t)(opp(I) * CELLS + c)
+                                : (k == 13 ? (uint32_t)(I * CELLS + lc) : base + (uint32_t)(I * CELLS + lc)));
+        inside |= (uint32_t)in << I;
+    });
+    float2 v[Q];
+    Unroll<0, Q>::run([&]<int I>() {
+        if (!live)
+            v[I] = make_float2(0.f, 0.f);
+        else if ((inside >> I) & 1u)
+            v[I] = make_float2(st[off[I]], st[off[I] + Q * CELLS]);
+        else
+            v[I] = make_float2(__ldg(rd + off[I]), __ldg(rd + off[I] + Q * CELLS));
+    });
+    sink.template operator()<0>(v[0]);
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        sink.template operator()<pair_rep(P)>(v[pair_rep(P)]);
+        sink.template operator()<opp(pair_rep(P))>(v[opp(pair_rep(P))]);
+    });
+}
+
+__device__ __forceinline__ void macro2_staged_body(const KParams &kp, int step, int criterion)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (criterion && ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;
+    staged_blocks(kp, rd, n, [&](int slot, int c, const float *st) {
+        const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
+        const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+        const bool live = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) return;
+        Moments2 m;
+        pull2_staged(wn, rd, st, c, bits, live, [&]<int I>(float2 v) { m.template add<I>(v); });
+        const float2 inv = make_float2(1.f / m.rho.x, 1.f / m.rho.y);
+        float u[2][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float2 ud = mul2(m.j[d], inv);
+            u[0][d] = ud.x;
+            u[1][d] = ud.y;
+        }
+        kp.mac[(size_t)slot * CELLS + c] =
+            live ? mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (criterion) criterion_mark<2>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
+    });
+}
+
+__global__ void __launch_bounds__(TMA_THREADS, 1) k_macro2_staged(KParams kp, int criterion)
+{
+    macro2_staged_body(kp, kp.ctrl->step, criterion);
+}
+
+template <bool TAU1>
+__device__ __forceinline__ void collide2_staged_body(const KParams &kp, int step)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par ^ 1];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 7)) return;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;
+    float *wr = kp.f + (size_t)(par ^ 1) * kp.buf_stride;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->cell_updates += (unsigned long long)n * CELLS;
+        ctrl->fluid_updates += ctrl->fluid_active;
+    }
+    staged_blocks(kp, rd, n, [&](int slot, int c, const float *st) {
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
+        const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+        const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+        // every lane takes part in the ballot (it must not sit behind &&)
+        const bool row_live = row_has(live);
+        const bool fill = (bits & 1u) && row_live;  // solid cell completing a sector
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) return;
+        Moments2 m;
+        float2 fin[TAU1 ? 1 : Q];
+        pull2_staged(wn, rd, st, c, bits, live, [&]<int I>(float2 v) {
+            m.template add<I>(v);
+            if constexpr (!TAU1) fin[I] = v;
+        });
+        const float2 rho = m.rho;
+        const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+        float2 u[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
+        float2 F[3];
+        forces2<2>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
+        if (!live && !fill) return;
+        float2 v[3], nv[3], nu[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            v[d] = fma2(F[d], inv, u[d]);
+            nv[d] = sub2(make_float2(0.f, 0.f), v[d]);
+            nu[d] = sub2(make_float2(0.f, 0.f), u[d]);
+        }
+        const float2 one = splat(1.f);
+        const float2 cv = fma2(splat(-1.5f), fma2(v[0], v[0], fma2(v[1], v[1], mul2(v[2], v[2]))), one);
+        const float2 cu = fma2(splat(-1.5f), fma2(u[0], u[0], fma2(u[1], u[1], mul2(u[2], u[2]))), one);
+        float2 wrho[3];
+        Unroll<0, 3>::run([&]<int K>() {
+            constexpr int I = K == 0 ? 0 : (K == 1 ? 1 : 5);
+            wrho[K] = mul2(splat(wgt(I)), rho);
+        });
+        const float2 relax = splat(1.f - kp.omega);
+        float2 moving = make_float2(0.f, 0.f);
+        float *d0 = wr + (size_t)slot * kp.slot_floats + c;
+        float *d1 = d0 + Q * CELLS;
+        Unroll<1, Q>::run([&]<int I>() {
+            const float2 ev = edot<I>(v, nv);
+            float2 f = mul2(wrho[wclass(I)], fma2(ev, fma2(ev, splat(4.5f), splat(3.f)), cv));
+            if constexpr (!TAU1) {
+                const float2 eu = edot<I>(u, nu);
+                const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
+                f = fma2(relax, sub2(fin[I], e0), f);
+            }
+            moving = add2(moving, f);
+            d0[I * CELLS] = live ? f.x : 0.f;
+            d1[I * CELLS] = live ? f.y : 0.f;
+        });
+        const float2 rest = sub2(rho, moving);
+        d0[0] = live ? rest.x : 0.f;
+        d1[0] = live ? rest.y : 0.f;
+        (void)cu;
+        if (live && kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+            float *up = kp.uprev + (size_t)slot * 2 * 3 * CELLS + c;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                up[d * CELLS] = u[d].x;
+                up[(3 + d) * CELLS] = u[d].y;
+            }
+        }
+    });
+}
+
+template <bool TAU1>
+__global__ void __launch_bounds__(TMA_THREADS, 1) k_collide2_staged(KParams kp)
+{
+    const int step = *(volatile const int *)&kp.ctrl->step;
+    collide2_staged_body<TAU1>(kp, step);
+    step_done(kp.ctrl, step);
+}
+
 // Pass 2 of a step in the deviation forms (as k_collide, paired arithmetic
 // for the two components).  Every value
 // is stored against the density its reader has now: the neighbour's mac of
@@ -1970,6 +2224,25 @@ cudaError_t launch_persistent(int sms, cudaStream_t s, A... args)
     return cudaGetLastError();
 }
 
+// Launch of a TMA-staged kernel: one CTA of TMA_THREADS per resident slot,
+// TMA_SMEM bytes of dynamic shared memory (opted in once per kernel).
+template <auto Kern, class... A>
+cudaError_t launch_staged(int sms, cudaStream_t s, A... args)
+{
+    static int occ = 0;
+    if (!occ) {
+        cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM);
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Kern, TMA_THREADS, TMA_SMEM) != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+        }
+        occ = n > 0 ? n : 1;
+    }
+    Kern<<<sms * occ, TMA_THREADS, TMA_SMEM, s>>>(args...);
+    return cudaGetLastError();
+}
+
 template <int ST>
 struct Launch {
     static cudaError_t init(const KParams &kp, const float *in_block, int slot0, int nslots, int grid,
@@ -2000,6 +2273,7 @@ struct Launch {
             if (kp.ncomp == 2) return launch_persistent<k_macro_dev<2, ST>>(sms, s, kp, criterion);
             return launch_persistent<k_macro_dev<1, ST>>(sms, s, kp, criterion);
         } else {
+            if (kp.ncomp == 2 && kp.staged) return launch_staged<k_macro2_staged>(sms, s, kp, criterion);
             if (kp.ncomp == 2) return launch_persistent<k_macro2>(sms, s, kp, criterion);
             return launch_persistent<k_macro<1>>(sms, s, kp, criterion);
         }
@@ -2023,6 +2297,10 @@ struct Launch {
             if (tau1) return launch_persistent<k_collide_dev<1, true, ST>>(sms, s, kp);
             return launch_persistent<k_collide_dev<1, false, ST>>(sms, s, kp);
         } else {
+            if (kp.ncomp == 2 && kp.staged) {
+                if (tau1) return launch_staged<k_collide2_staged<true>>(sms, s, kp);
+                return launch_staged<k_collide2_staged<false>>(sms, s, kp);
+            }
             if (kp.ncomp == 2) {
                 if (tau1) return launch_persistent<k_collide2<true>>(sms, s, kp);
                 return launch_persistent<k_collide2<false>>(sms, s, kp);

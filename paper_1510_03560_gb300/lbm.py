@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm_checked.so" if os.environ.get("LBM_CHECKED
                         else "liblbm.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, 1, 2, 3, 4, 5
-EXEC = {"stream": 0, "graph": 1, "persistent": 2}  # LBM_EXEC_*
+EXEC = {"stream": 0, "graph": 1, "persistent": 2, "staged": 3}  # LBM_EXEC_*
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}  # LBM_STORAGE_*
 Q = 19
 EDGE = 8
@@ -344,7 +344,7 @@ def _lbm_set_proposer(self, mlp, period=16, threshold=0.5):
 
 
 def _lbm_set_exec(self, mode):
-    """"stream", "graph" or "persistent" (or the LBM_EXEC_* code)."""
+    """"stream", "graph", "persistent" or "staged" (or the LBM_EXEC_* code)."""
     self._check(self.lib.lbm_set_exec(self.h, EXEC[mode] if isinstance(mode, str) else int(mode)))
 
 

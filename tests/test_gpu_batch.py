@@ -48,5 +48,5 @@ def test_batch_members_match_solo_runs(L, mode):
 def test_autotune_reports_every_mode(L):
     batch, _ = B.pack(_cases())
     best, times = B.autotune(L, batch, steps=10)
-    assert best in times and set(times) == {"stream", "graph", "persistent"}
+    assert best in times and set(times) == {"stream", "graph", "persistent", "staged"}
     assert all(t > 0 for t in times.values())

@@ -45,7 +45,7 @@ def test_modes_agree_bit_for_bit(L, which, storage):
                                   r_range=(3.0, 6.0), S=1e-4)
     chunks = [7, 20, 1, 32]  # odd and even counts: graph pairs plus single steps
     ref = _run(L, case, "stream", chunks, storage=storage)
-    for mode in ("graph", "persistent"):
+    for mode in ("graph", "persistent", "staged"):
         got = _run(L, case, mode, chunks, storage=storage)
         for a, b in zip(ref[0], got[0]):
             np.testing.assert_array_equal(a, b)
@@ -57,10 +57,11 @@ def test_modes_agree_bit_for_bit(L, which, storage):
         np.testing.assert_allclose(got[3], ref[3], rtol=1e-12)
 
 
-def test_persistent_static_mode(L):
+@pytest.mark.parametrize("mode", ["persistent", "staged"])
+def test_static_mode(L, mode):
     case = W.drop_in_box(progressive=0)
     ref = _run(L, case, "stream", [15])
-    got = _run(L, case, "persistent", [15])
+    got = _run(L, case, mode, [15])
     for fa, fb in zip(ref[1], got[1]):
         for x, y in zip(fa, fb):
             np.testing.assert_array_equal(x, y)
