@@ -926,7 +926,9 @@ __device__ __forceinline__ void macro_dev_body(const KParams &kp, int step, int 
                 bits2 = kp.nbits[(size_t)(it3 / PARTS) * CELLS + (it3 % PARTS) * THREADS + threadIdx.x];
             }
         }
-        if (cur.ok) {
+        // (every lane votes: the collective must not sit behind &&)
+        const bool any_cell = __any_sync(FULL, !(cur.bits & 1u));
+        if (cur.ok && any_cell) {  // skip warps of solid cells only
             const bool live = !(cur.bits & 1u);
             const bool held = (cur.bits >> HELD_BIT) & 1u;
             float2 wref[3], famb[3];
@@ -1787,7 +1789,9 @@ __device__ __forceinline__ void collide_dev_body(const KParams &kp, int step)
             next_row = nbr_row_lane(kp, it2 / PARTS);
             next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
-        if (cur.ok) {
+        // (every lane votes: the collective must not sit behind &&)
+        const bool any_cell = __any_sync(FULL, !(cur.bits & 1u));
+        if (cur.ok && any_cell) {  // skip warps of solid cells only
             const int slot = cur.slot, c = cur.c;
             const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
             const uint32_t bits = cur.bits;
