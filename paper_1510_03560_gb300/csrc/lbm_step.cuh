@@ -960,6 +960,59 @@ __global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KPara
     macro_dev_body<NC, ST>(kp, kp.ctrl->step, criterion);
 }
 
+// Deterministic compaction of the candidates of a step (one CTA): the
+// criterion marks candidates in any order (cand_mark 1, a provisional slot);
+// here they are renumbered in ascending block order, slot n_old + rank, by
+// a prefix scan over the marks (each thread counts a contiguous range of
+// block ids, a warp-shuffle scan and a scan of the warp totals give each
+// range its first rank).  Block creation then sets the mark to 2 (meshed).
+// Nothing is done when the pool cannot hold the candidates (block creation
+// undoes them).  Every thread of the CTA must call.
+__device__ __forceinline__ void order_body(const KParams &kp, int step)
+{
+    __shared__ int warp_sum[32];
+    Ctrl *ctrl = kp.ctrl;
+    const int par = step & 1;
+    const int n_old = ctrl->n_active[par];
+    const int ncand = ctrl->ncand[par];
+    if (ctrl->status || ncand <= 0 || n_old + ncand > kp.capacity) return;
+    const int nb = kp.nbx * kp.nby * kp.nbz;
+    const int T = blockDim.x, t = threadIdx.x;
+    const int chunk = (nb + T - 1) / T;
+    const int lo = min(nb, t * chunk), hi = min(nb, lo + chunk);
+    int cnt = 0;
+    for (int b = lo; b < hi; ++b) cnt += kp.cand_mark[b] == 1u;
+    // exclusive prefix of cnt over the CTA
+    const int lane = t & 31, warp = t >> 5;
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < (T >> 5) ? warp_sum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += v;
+        }
+        warp_sum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    int r = (warp ? warp_sum[warp - 1] : 0) + incl - cnt;
+    for (int b = lo; b < hi; ++b) {
+        if (kp.cand_mark[b] != 1u) continue;
+        kp.cand_list[r] = b;
+        kp.slot_of[b] = n_old + r;
+        ++r;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_order(KParams kp) { order_body(kp, kp.ctrl->step); }
+
 // Block creation (Sec. 4.2-4.3): the candidates found by k_macro get slots
 // after the meshed ones, start from the ambient resting equilibrium in both
 // buffers (R14) and get their streaming and moments of this step computed,
@@ -1006,7 +1059,10 @@ __device__ __forceinline__ void activate_body(const KParams &kp, int step)
         const int slot = n_old + k;
         const int gid = kp.cand_list[k];
         if (!in_range(kp, gid, (long long)kp.nbx * kp.nby * kp.nbz, 5)) continue;
-        if (c == 0) kp.block_of[slot] = gid;
+        if (c == 0) {
+            kp.block_of[slot] = gid;
+            kp.cand_mark[gid] = 2u;  // meshed
+        }
         if (c < 32) {
             // the new block's row of the neighbour-slot table, and its slot in
             // the rows of its meshed neighbours (every candidate's slot is
@@ -2194,6 +2250,8 @@ __global__ void __launch_bounds__(THREADS, (Phases<NC, TAU1, ST>::MIN_CTAS)) k_r
         P::macro(kp, step, progressive);
         if (!grid_sync(ctrl, gridDim.x, kp.barrier_spins)) return;
         if (progressive) {
+            if (blockIdx.x == 0) order_body(kp, step);
+            if (!grid_sync(ctrl, gridDim.x, kp.barrier_spins)) return;
             activate_body<NC, ST>(kp, step);
             if (!grid_sync(ctrl, gridDim.x, kp.barrier_spins)) return;
         }
@@ -2284,6 +2342,8 @@ struct Launch {
     }
     static cudaError_t activate(const KParams &kp, int step, int sms, cudaStream_t s)
     {
+        k_order<<<1, 1024, 0, s>>>(kp);
+        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
         if (kp.ncomp == 2)
             k_activate<2, ST><<<sms, THREADS, 0, s>>>(kp);
         else
