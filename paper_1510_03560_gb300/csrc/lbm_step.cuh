@@ -1015,7 +1015,9 @@ __global__ void __launch_bounds__(1024) k_order(KParams kp) { order_body(kp, kp.
 
 // Block creation (Sec. 4.2-4.3): the candidates found by k_macro get slots
 // after the meshed ones, start from the ambient resting equilibrium in both
-// buffers (R14) and get their streaming and moments of this step computed,
+// buffers (the paper gives no state for a new sub-domain; the resting
+// ambient keeps an untouched region unchanged) and get their streaming and
+// moments of this step computed,
 // with every block created in this step seen as ambient.  The deviation
 // forms write the read buffer only (the collision of this step writes every
 // non-solid cell of the other one), against the previous densities of the
@@ -1211,7 +1213,8 @@ __device__ __forceinline__ void forces(const KParams &kp, const WarpNbr &wn, uin
 }
 
 // Pass 2 of a step (FP32 form): streaming again, forces, forced BGK
-// collision (Eqs. 10-12, R1 sign), store into the other buffer; the
+// collision (Eqs. 10-12, read with the stable sign -(f - f_eq) / tau of
+// standard BGK), store into the other buffer; the
 // velocity is kept for the next criterion at cells that border unmeshed
 // blocks.
 template <int NC, bool TAU1>
@@ -1947,7 +1950,8 @@ __global__ void __launch_bounds__(THREADS, DEV_COLLIDE_MIN_CTAS) k_collide_dev(K
 
 // Macroscopic output of one component for slots [slot0, slot0 + nslots):
 // out[slot - slot0][4][CELLS] = rho, ux, uy, uz, velocity u + F / (2 rho)
-// at fluid cells (R9), own moments at held cells, zeros at solid cells.
+// at fluid cells (the exact-difference forcing's physical velocity), own
+// moments at held cells, zeros at solid cells.
 // Expects mac of this step (k_macro without the criterion).
 template <int NC, int ST>
 __global__ void __launch_bounds__(THREADS) k_output(KParams kp, int rdbuf, int comp, int slot0,

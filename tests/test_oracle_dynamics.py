@@ -208,7 +208,7 @@ def state_with_ambient(s, amb, block):
 
 
 def test_progressive_equals_static():
-    """With S = 0 and a bit-stationary ambient (R14), meshing blocks only
+    """With S = 0 and a bit-stationary ambient (new blocks start at rest in it), meshing blocks only
     where Eq. 13 fires reproduces the static mesh exactly at every step,
     while far blocks stay unmeshed for a while."""
     amb = (fixed_point(W.f32(W.RHO_VAP)), fixed_point(1.0))

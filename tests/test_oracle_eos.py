@@ -153,7 +153,7 @@ def test_cross_force_sign_and_balance():
 
 
 def test_adhesion_sign():
-    """Fluid-solid force (R8): with g_ads < 0 liquid next to a wall is pulled
+    """Fluid-solid force: with g_ads < 0 liquid next to a wall is pulled
     towards it; at or below the ambient density it feels nothing."""
     n = 16
     ct = np.zeros((n, 8, 8), np.uint8)
