@@ -155,11 +155,11 @@ def make_case(S=None, size=256, workload="injection"):
 
 
 def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32", proposer=None,
-              exec_mode="stream"):
+              exec_mode="stream", streaming="ab"):
     """Warm up, then time `steps` steps one by one (L2 flushed before each).
     proposer: an lbm MLP to run the activation proposer with (period 16,
-    threshold 0.5)."""
-    sim = L.from_case(case, progressive=progressive, storage=storage)
+    threshold 0.5).  streaming: "ab" or "aa" (one population array)."""
+    sim = L.from_case(case, progressive=progressive, storage=storage, streaming=streaming)
     sim.set_exec(exec_mode)
     if proposer is not None:
         sim.set_proposer(proposer, period=16, threshold=0.5)
@@ -194,20 +194,21 @@ def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="
         prepared_hits=st1["prepared_hits"] - st0["prepared_hits"],
         nonsolid_blocks=st1["nonsolid_blocks"],
         total_blocks=st1["total_blocks"],
+        device_bytes=st1["device_bytes"],
         clocks=clk.summary(),
     )
     sim.close()
     return out
 
 
-def run_e2e(L, torch, case, steps, storage="fp32"):
+def run_e2e(L, torch, case, steps, storage="fp32", streaming="ab"):
     """End to end through the public API with host buffers: geometry and
     initial state uploaded, `steps` steps, both components' fields read
     back; wall clock around all of it."""
     import numpy as np
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim = L.from_case(case, storage=storage)
+    sim = L.from_case(case, storage=storage, streaming=streaming)
     sim.step(steps)
     outs = [sim.macro(a) for a in range(2)]
     torch.cuda.synchronize()
@@ -376,8 +377,10 @@ def main():
                          "quoted on")
     ap.add_argument("--exec", default="stream", choices=["stream", "graph", "persistent", "staged"],
                     help="how the library enqueues the steps")
+    ap.add_argument("--streaming", default="ab", choices=["ab", "aa"],
+                    help="population streaming pattern: two arrays (A-B) or one updated in place (A-A)")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip timing the FP16, BF16 and learned-proposer forms")
+                    help="skip timing the FP16, BF16, A-A and learned-proposer forms")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -401,7 +404,7 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if args.static_only:
         st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage,
-                       exec_mode=args.exec)
+                       exec_mode=args.exec, streaming=args.streaming)
         if rank == 0:
             print(json.dumps({"static_mlups": st["cells"] / (st["ms"] * 1e-3) / 1e6,
                               "ms": st["ms"], "kernel_ms": st["kernel_ms"],
@@ -412,7 +415,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, args.storage,
-                     exec_mode=args.exec)
+                     exec_mode=args.exec, streaming=args.streaming)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -420,11 +423,19 @@ def main():
 
     stat = None
     if not args.no_static:
-        stat = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage)
+        stat = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage,
+                         streaming=args.streaming)
         s_max, s_cells = reduce_max_sum(dist, torch, stat["ms"], stat["cells"])
     forms = {}
-    if not args.no_forms and args.storage == "fp32":
+    if not args.no_forms and args.storage == "fp32" and args.streaming == "ab":
         from paper_1510_03560_gb300 import proposer as PR
+        r = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, "fp32", streaming="aa")
+        f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
+        forms["aa"] = {"mlups": round(f_cells / (f_max * 1e-3) / 1e6, 1),
+                       "collide_ms_per_step": round(r["kernel_ms"][2] / args.steps, 5),
+                       "macro_ms_per_step": round(r["kernel_ms"][0] / args.steps, 5),
+                       "device_bytes": r["device_bytes"], "device_bytes_ab": prog["device_bytes"],
+                       "streaming": "A-A: one population array updated in place"}
         for form in ("fp16", "bf16"):
             r = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, form)
             f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
@@ -441,7 +452,8 @@ def main():
             "activate_ms_per_step_without": round(prog["kernel_ms"][1] / args.steps, 5),
             "period": 16, "threshold": 0.5, "inference": "bf16 operands, fp32 accumulation"}
         mlp.close()
-    e2e = None if args.no_e2e else run_e2e(L, torch, case, args.warmup + args.steps, args.storage)
+    e2e = None if args.no_e2e else run_e2e(L, torch, case, args.warmup + args.steps, args.storage,
+                                           args.streaming)
     if e2e is not None:
         e_max, e_cells = reduce_max_sum(dist, torch, e2e["wall"], e2e["cells"])
 
@@ -459,7 +471,7 @@ def main():
     # dominant kernel: force + collide (kind 2)
     kms, kn = prog["kernel_ms"][2], prog["kernel_launches"][2]
     coll_gbs = prog["fluid"] * bpu / (kms * 1e-3) / 1e9 if kms > 0 else None
-    traffic_pc = kernel_traffic(args.storage)
+    traffic_pc = kernel_traffic(args.storage) if args.streaming == "ab" else None
     avg_cells = prog["cells"] / max(kn, 1)
     avg_fluid = prog["fluid"] / max(kn, 1)
     roofline = {
@@ -467,7 +479,9 @@ def main():
         "peak": peak, "unit": "GB/s",
         "frac": round(coll_gbs / peak, 4) if coll_gbs else None,
         "traffic": round(traffic_pc * avg_cells) if traffic_pc else None,
-        "kernel": "k_collide (force gather + exact-difference collision + pull streaming)",
+        "kernel": ("k_collide (force gather + exact-difference collision + pull streaming)"
+                   if args.streaming == "ab" else
+                   "k_collide_aa (force gather + exact-difference collision, A-A in place)"),
         "peak_kind": peak_kind,
         "algorithmic_bytes_per_launch": round(avg_fluid * bpu),
         "avg_launch_ms": round(kms / max(kn, 1), 5),
@@ -478,7 +492,7 @@ def main():
         "workload": (WORKLOADS[args.workload][0] if args.workload in WORKLOADS
                      else WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}"),
         "mode": "progressive", "grid": [case["params"][k] for k in ("nx", "ny", "nz")], "block": [8, 8, 8],
-        "storage": args.storage, "exec": args.exec,
+        "storage": args.storage, "exec": args.exec, "streaming": args.streaming,
         "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
         "mean_active_fraction": round(prog["cells"] / 512 / args.steps / prog["total_blocks"], 4),

@@ -78,6 +78,15 @@ extern "C" {
 #define LBM_STORAGE_FP16 1 /* IEEE binary16 deviations */
 #define LBM_STORAGE_BF16 2 /* bfloat16 deviations */
 
+/* Streaming pattern of the populations (lbm_params.streaming; Sec. 3
+ * compares the A-B pattern, two arrays read and written alternately, with
+ * the A-A pattern, one array updated in place, which the paper uses to
+ * halve the memory of the populations).  Both give the same results bit for
+ * bit.  A-A needs the FP32 storage form with two components and the STREAM
+ * or GRAPH execution mode. */
+#define LBM_STREAM_AB 0
+#define LBM_STREAM_AA 1
+
 #define LBM_BLOCK_EDGE 8 /* cells per block edge */
 #define LBM_Q 19         /* D3Q19 populations per component */
 
@@ -96,6 +105,7 @@ typedef struct lbm_params {
     int progressive;     /* 1: progressive mesh (Sec. 4); 0: static mesh, every
                             block holding a non-solid cell meshed from the start */
     int storage;         /* LBM_STORAGE_FP32 (0), _FP16 or _BF16 */
+    int streaming;       /* LBM_STREAM_AB (0) or LBM_STREAM_AA */
     double tau;          /* BGK relaxation time, Eq. 1 (> 0.5) */
     double beta;         /* weighting term of Eq. 8 (the paper uses 1.16) */
     double pr_a, pr_b, pr_R, pr_omega; /* Peng-Robinson a, b, R, acentric factor, Eq. 7 */
@@ -136,11 +146,13 @@ typedef struct lbm_stats {
 } lbm_stats;
 
 /* Validate `p`, allocate the block pool (capacity x 2 buffers x ncomp x 19 x
- * 512 populations of 4 bytes, or 2 in the 16-bit storage forms) and the
- * tables, and return a new context in *out.  Allocates through p->dev_alloc
- * when given.  Errors: LBM_EINVAL (bad parameter: grid not a multiple of 8,
- * ncomp not 1 or 2, tau <= 0.5, S < 0, unknown storage form, ...; no CUDA
- * call is made then), LBM_ENOMEM, LBM_ECUDA.  On error *out is NULL. */
+ * 512 populations of 4 bytes, or 2 in the 16-bit storage forms; one buffer
+ * with A-A streaming) and the tables, and return a new context in *out.
+ * Allocates through p->dev_alloc when given.  Errors: LBM_EINVAL (bad
+ * parameter: grid not a multiple of 8, ncomp not 1 or 2, tau <= 0.5, S < 0,
+ * unknown storage form or streaming pattern, A-A streaming without the FP32
+ * form and two components, ...; no CUDA call is made then), LBM_ENOMEM,
+ * LBM_ECUDA.  On error *out is NULL. */
 int lbm_create(const lbm_params *p, lbm_ctx **out);
 
 /* Free everything the context holds.  NULL is accepted. */

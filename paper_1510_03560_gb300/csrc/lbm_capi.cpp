@@ -56,7 +56,9 @@ struct lbm_ctx {
     KParams kp{};
     // device allocations
     std::vector<void *> allocs;
+    std::vector<size_t> alloc_sizes;  // bytes of each entry of allocs
     long long device_bytes = 0;
+    int held_rows = 0;                // rows of kp.held_f (A-A streaming)
     double *mass_partial = nullptr;
     double *mass_out = nullptr;
     float *stage = nullptr;    // staging buffer (initial state upload, macro download)
@@ -144,6 +146,7 @@ void *dev_alloc(lbm_ctx *c, size_t bytes)
     }
     if (ptr) {
         c->allocs.push_back(ptr);
+        c->alloc_sizes.push_back(bytes);
         c->device_bytes += (long long)bytes;
     }
     return ptr;
@@ -158,7 +161,25 @@ void free_all(lbm_ctx *c)
             cudaFreeAsync(ptr, c->stream);
     }
     c->allocs.clear();
+    c->alloc_sizes.clear();
     c->device_bytes = 0;
+}
+
+// Free one allocation of the context (NULL is accepted).
+void release(lbm_ctx *c, void *ptr)
+{
+    if (!ptr) return;
+    for (size_t i = 0; i < c->allocs.size(); ++i)
+        if (c->allocs[i] == ptr) {
+            c->device_bytes -= (long long)c->alloc_sizes[i];
+            c->allocs.erase(c->allocs.begin() + (long)i);
+            c->alloc_sizes.erase(c->alloc_sizes.begin() + (long)i);
+            if (c->p.dev_free)
+                c->p.dev_free(ptr, c->p.alloc_user);
+            else
+                cudaFreeAsync(ptr, c->stream);
+            break;
+        }
 }
 
 int validate(const lbm_params *p)
@@ -177,6 +198,10 @@ int validate(const lbm_params *p)
     if (p->storage != LBM_STORAGE_FP32 && p->storage != LBM_STORAGE_FP16 &&
         p->storage != LBM_STORAGE_BF16)
         return fail(nullptr, LBM_EINVAL, "unknown storage form %d", p->storage);
+    if (p->streaming != LBM_STREAM_AB && p->streaming != LBM_STREAM_AA)
+        return fail(nullptr, LBM_EINVAL, "unknown streaming pattern %d", p->streaming);
+    if (p->streaming == LBM_STREAM_AA && (p->storage != LBM_STORAGE_FP32 || p->ncomp != 2))
+        return fail(nullptr, LBM_EINVAL, "A-A streaming needs the FP32 storage form and two components");
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
         return fail(nullptr, LBM_EINVAL, "dev_alloc and dev_free must be given together");
     for (int a = 0; a < 3; ++a)
@@ -464,17 +489,22 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
     KParams &k = c->kp;
     k.slot_floats = (int)slot_floats;
     k.amb_slot = c->capacity;
-    k.buf_stride = slot_floats * (size_t)(c->capacity + 1);
-    if (k.buf_stride >= (1ull << 32)) {
+    const size_t one_buf = slot_floats * (size_t)(c->capacity + 1);
+    if (one_buf >= (1ull << 32)) {
         fail(c, LBM_EINVAL, "block pool of %d blocks too large for 32-bit offsets", c->capacity);
         return bail(LBM_EINVAL);
     }
+    // A-A streaming: one array, addressed by both parities (stride 0)
+    const bool aa = p->streaming == LBM_STREAM_AA;
+    k.aa = aa ? 1 : 0;
+    k.buf_stride = aa ? 0 : one_buf;
     struct Want {
         void **dst;
         size_t bytes;
     } want[] = {
-        {(void **)&k.f, dev16 ? 0 : 2 * k.buf_stride * sizeof(float)},
-        {(void **)&k.h, dev16 ? 2 * k.buf_stride * sizeof(uint32_t) : 0},
+        {(void **)&k.f, dev16 ? 0 : (aa ? 1 : 2) * one_buf * sizeof(float)},
+        {(void **)&k.h, dev16 ? 2 * one_buf * sizeof(uint32_t) : 0},
+        {(void **)&k.held_rank, aa ? (size_t)c->nblocks * sizeof(int) : 0},
         {(void **)&k.mac, (dev16 ? 2 : 1) * (size_t)(c->capacity + 1) * CELLS * sizeof(float4)},
         {(void **)&k.nbits, (size_t)c->capacity * CELLS * sizeof(uint32_t)},
         {(void **)&k.nbr, (size_t)c->capacity * NBR_STRIDE * sizeof(int)},
@@ -639,6 +669,29 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
         CUDA_OR_FAIL(c, cudaMemcpyAsync(k.block_of, block_of.data(), n0 * sizeof(int), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.solid, c->solid_h.data(), nb * MASK_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.held, c->held_h.data(), nb * MASK_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    if (k.aa) {
+        // A-A: a row of constant populations for every block holding held cells
+        std::vector<int> rank(nb, -1);
+        int nheld = 0;
+        for (long long b = 0; b < nb; ++b)
+            for (int w = 0; w < MASK_WORDS; ++w)
+                if (c->held_h[b * MASK_WORDS + w]) {
+                    rank[b] = nheld++;
+                    break;
+                }
+        if (nheld > c->held_rows) {
+            CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+            release(c, k.held_f);
+            k.held_f = (float *)dev_alloc(c, (size_t)nheld * k.slot_floats * sizeof(float));
+            if (!k.held_f) {
+                c->held_rows = 0;
+                return fail(c, LBM_ENOMEM, "device allocation of the held-cell table failed");
+            }
+            c->held_rows = nheld;
+        }
+        CUDA_OR_FAIL(c, cudaMemcpyAsync((void *)k.held_rank, rank.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+        CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
+    }
     CUDA_OR_FAIL(c, cudaMemsetAsync(k.cand_mark, 0, nb * sizeof(unsigned), s));
     {
         std::vector<int> act(nb, -1);
@@ -837,9 +890,10 @@ int lbm_get_block_populations(lbm_ctx *c, int32_t block_id, float *out)
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
     if (slot < 0) return fail(c, LBM_EINVAL, "block %d is not meshed", block_id);
     const int rd = (int)(c->step & 1);
-    const float *src = c->kp.f ? c->kp.f + (size_t)rd * c->kp.buf_stride + (size_t)slot * c->kp.slot_floats
+    const bool gather = !c->kp.f || c->kp.aa;  // 16-bit forms decode, A-A gathers
+    const float *src = !gather ? c->kp.f + (size_t)rd * c->kp.buf_stride + (size_t)slot * c->kp.slot_floats
                                : c->stage;
-    if (!c->kp.f) {
+    if (gather) {
         CUDA_OR_FAIL(c, launch_block_pops(c->kp, rd, slot, c->stage, c->stream));
         c->launches += 1;
     }
@@ -1006,6 +1060,8 @@ int lbm_set_exec(lbm_ctx *c, int mode)
         mode != LBM_EXEC_STAGED)
         return fail(c, LBM_EINVAL, "unknown execution mode %d", mode);
     DeviceGuard g(c->device);
+    if (c->kp.aa && (mode == LBM_EXEC_PERSISTENT || mode == LBM_EXEC_STAGED))
+        return fail(c, LBM_EINVAL, "A-A streaming runs in the STREAM and GRAPH modes");
     if (mode == LBM_EXEC_PERSISTENT) {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device);

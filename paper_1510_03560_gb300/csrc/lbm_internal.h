@@ -66,6 +66,7 @@ struct KParams {
     float famb[2][Q];   // ambient resting populations w_i rho_amb
     // device memory
     float *f;           // FP32 form: [2][capacity + 1][ncomp][Q][CELLS]
+                        // (one buffer with A-A streaming)
     uint32_t *h;        // 16-bit forms: [2][capacity + 1][Q][CELLS] words of
                         // two 16-bit deviations from w_i rho of the reading
                         // cell (component 0 low, component 1 high)
@@ -89,11 +90,18 @@ struct KParams {
     const unsigned *prep;       // [nblocks] or NULL: 1 once nbits_pre holds the block's words
     const uint32_t *nbits_pre;  // [nblocks][CELLS]: solid words prepared by the proposer
     Ctrl *ctrl;
-    size_t buf_stride;  // elements (floats or words) per population buffer
+    size_t buf_stride;  // elements (floats or words) per population buffer;
+                        // 0 with A-A streaming
     int slot_floats;    // elements per slot: ncomp * Q * CELLS (FP32) or
                         // Q * CELLS (16-bit forms)
     long long barrier_spins;  // bounded wait of a grid barrier or a bulk copy (polls)
     int staged;         // FP32, two components: TMA-staged pass kernels
+    // A-A streaming (FP32, two components): one population array (f, with
+    // buf_stride 0, so that both parities address it), updated in place
+    int aa;
+    float *held_f;          // [held blocks][2][Q][CELLS]: the constant
+                            // populations of held cells (A-A only)
+    const int *held_rank;   // [nblocks]: row of held_f, -1 without held cells
 };
 
 // Kernel kinds for per-kernel timing.

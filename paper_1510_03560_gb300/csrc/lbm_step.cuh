@@ -587,6 +587,127 @@ __device__ __forceinline__ void dev_consume2(const DevLoad &L, const float2 wref
     });
 }
 
+// ---- A-A streaming: addressing (FP32, two components) ----------------------
+// One population array updated in place (the A-A pattern of Sec. 3).  Step t
+// is a neighbour step when t is even and a local step when t is odd:
+//   neighbour step: the population arriving at x along e_i is read at
+//     (x - e_i, slot opp(i)); the value leaving x along e_i is written to
+//     (x + e_i, slot i);
+//   local step: read at (x, slot i), written to (x, slot opp(i)).
+// In a step every location is read and written by one cell only, so the
+// update is in place.  Halfway bounce-back: a neighbour step reads (x, i)
+// when x - e_i is solid and writes (x, opp(i)) when x + e_i is solid; a
+// local step needs no case.  Unmeshed source blocks give the ambient
+// equilibrium (the ambient slot).  A neighbour step's value leaving towards
+// an unmeshed block is parked at (x, opp(i)), a location no other cell
+// reads or writes in that step.  A block created in a local step takes the
+// parked values of its meshed neighbours as its incoming populations (the
+// values the A-B pull reads from their buffers); one created in a neighbour
+// step starts from the ambient equilibrium in every slot.  In a local step's
+// collision, blocks created in the same step are ambient sources (their
+// slots now hold their own incoming values).  Held cells keep their
+// constant populations in held_f and write them like any other cell.  The
+// initial state is laid out as after a local step: f_i(x) at (x, opp(i)).
+// The values and the arithmetic order are those of the A-B kernels, so the
+// results are the same bit for bit.
+
+// Offset (component 0; component 1 is Q * CELLS further) of the population
+// arriving along e_I at the cell (lx, ly, lz) in an A-A step.  own = slot *
+// slot_floats + c, amb_own = amb_slot * slot_floats + c; fresh: the
+// warp-uniform mask of neighbour blocks created in this step (the
+// collision of a local step).  Every lane calls (a shuffle in neighbour
+// steps).
+template <bool LOCAL, int I>
+__device__ __forceinline__ uint32_t aa_src(const WarpNbr &wn, uint32_t own, uint32_t amb_own, int lx,
+                                           int ly, int lz, uint32_t bits, unsigned fresh)
+{
+    const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+    const int k = nbk(sx, sy, sz);
+    const bool solid = (bits >> I) & 1u;
+    if constexpr (LOCAL) {
+        const bool ambient = !solid && (((wn.amb | fresh) >> k) & 1u);
+        return (ambient ? amb_own : own) + (uint32_t)(I * CELLS);
+    } else {
+        const int lc = lcell(sx, sy, sz);
+        const uint32_t base = __shfl_sync(FULL, wn.fbase, k);
+        return solid ? own + (uint32_t)(I * CELLS) : base + (uint32_t)(opp(I) * CELLS + lc);
+    }
+}
+
+// Offset of the location that receives the value leaving the cell along e_I
+// in an A-A step.  Every lane calls (a shuffle in neighbour steps).
+template <bool LOCAL, int I>
+__device__ __forceinline__ uint32_t aa_dst(const WarpNbr &wn, uint32_t own, int lx, int ly, int lz,
+                                           uint32_t bits)
+{
+    if constexpr (LOCAL || I == 0) {
+        return own + (uint32_t)(opp(I) * CELLS);
+    } else {
+        const int tx = lx + cx(I), ty = ly + cy(I), tz = lz + cz(I);
+        const int k = nbk(tx, ty, tz), lc = lcell(tx, ty, tz);
+        const uint32_t base = __shfl_sync(FULL, wn.fbase, k);
+        const bool park = ((bits >> opp(I)) & 1u) || ((wn.amb >> k) & 1u);
+        return park ? own + (uint32_t)(opp(I) * CELLS) : base + (uint32_t)(I * CELLS + lc);
+    }
+}
+
+// The pull of one cell in an A-A step, handing both components of each
+// direction to sink(I, (f_0, f_1)) in pull2_f32's order.  Held cells read
+// their constants.  All lanes call; `live` masks the loads.
+template <bool LOCAL, class Sink>
+__device__ __forceinline__ void pull2_aa(const KParams &kp, const WarpNbr &wn, int own_slot, int c, int lx,
+                                         int ly, int lz, uint32_t bits, bool live, unsigned fresh, Sink &&sink)
+{
+    const bool held = (bits >> HELD_BIT) & 1u;
+    const uint32_t own = (uint32_t)own_slot * (uint32_t)kp.slot_floats + (uint32_t)c;
+    const uint32_t amb_own = (uint32_t)kp.amb_slot * (uint32_t)kp.slot_floats + (uint32_t)c;
+    const float *src = kp.f;
+    uint32_t hown = 0;
+    if (held && live) {
+        src = kp.held_f;
+        hown = (uint32_t)kp.held_rank[kp.block_of[own_slot]] * (uint32_t)kp.slot_floats + (uint32_t)c;
+    }
+    uint32_t off[Q];
+    Unroll<0, Q>::run([&]<int I>() {
+        const uint32_t o = aa_src<LOCAL, I>(wn, own, amb_own, lx, ly, lz, bits, fresh);
+        off[I] = held ? hown + (uint32_t)(I * CELLS) : o;
+    });
+    float2 v[Q];
+    Unroll<0, Q>::run([&]<int I>() {
+        v[I] = live ? make_float2(__ldg(src + off[I]), __ldg(src + off[I] + Q * CELLS))
+                    : make_float2(0.f, 0.f);
+    });
+    sink.template operator()<0>(v[0]);
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        sink.template operator()<pair_rep(P)>(v[pair_rep(P)]);
+        sink.template operator()<opp(pair_rep(P))>(v[opp(pair_rep(P))]);
+    });
+}
+
+// pull() of the state a reader sees before the step of parity `par`, in the
+// A-A layout when the context streams that way (FP32, two components).
+template <int NC, int ST, class Sink>
+__device__ __forceinline__ void pull_state(const KParams &kp, const WarpNbr &wn,
+                                           const typename Store<ST>::T *rd, int par, int slot, int c,
+                                           int lx, int ly, int lz, uint32_t bits, bool live,
+                                           const float ref[2], Sink &&sink)
+{
+    if constexpr (!Store<ST>::DEV && NC == 2) {
+        if (kp.aa) {
+            auto two = [&]<int I>(float2 v) {
+                sink.template operator()<I>(0, v.x);
+                sink.template operator()<I>(1, v.y);
+            };
+            if (par)
+                pull2_aa<true>(kp, wn, slot, c, lx, ly, lz, bits, live, 0u, two);
+            else
+                pull2_aa<false>(kp, wn, slot, c, lx, ly, lz, bits, live, 0u, two);
+            return;
+        }
+    }
+    pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, ref, sink);
+}
+
 // First-pass values of a cell as stored in mac: (rho0, rho1, psi0, 0), so
 // that the two densities form one 8-byte pair.
 __device__ __forceinline__ float4 mac_pack(float rho0, float psi0, float rho1)
@@ -648,10 +769,19 @@ __global__ void __launch_bounds__(CELLS) k_init(KParams kp, const float *in, int
                 const float uu = ux * ux + uy * uy + uz * uz;
                 float *d0 = kp.f + (size_t)slot * kp.slot_floats + a * Q * CELLS + c;
                 float *d1 = d0 + kp.buf_stride;
+                // A-A: laid out as after a local step, held cells' constants in held_f
+                float *hc = kp.aa && ((bits >> HELD_BIT) & 1u)
+                                ? kp.held_f + (size_t)kp.held_rank[gid] * kp.slot_floats + a * Q * CELLS + c
+                                : nullptr;
                 Unroll<0, Q>::run([&]<int I>() {
                     const float v = feq<I>(wgt(I) * rho, ux, uy, uz, uu);
-                    d0[I * CELLS] = v;
-                    d1[I * CELLS] = v;
+                    if (kp.aa) {
+                        d0[opp(I) * CELLS] = v;
+                        if (hc) hc[I * CELLS] = v;
+                    } else {
+                        d0[I * CELLS] = v;
+                        d1[I * CELLS] = v;
+                    }
                 });
             }
             if (kp.uprev) {
@@ -963,13 +1093,16 @@ __global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KPara
 // Deterministic compaction of the candidates of a step (one CTA): the
 // criterion marks candidates in any order (cand_mark 1, a provisional slot);
 // here they are renumbered in ascending block order, slot n_old + rank, by
-// a prefix scan over the marks (each thread counts a contiguous range of
-// block ids, a warp-shuffle scan and a scan of the warp totals give each
-// range its first rank).  Block creation then sets the mark to 2 (meshed).
+// a prefix scan over the marks.  The marks go in tiles of 32 per thread: a
+// thread loads its 32 consecutive marks at once into a bit mask, a
+// warp-shuffle scan and a scan of the warp totals give its first rank, and
+// the candidates are written from the mask; a running total carries the
+// ranks from tile to tile.  Block creation then sets the mark to 2 (meshed).
 // Nothing is done when the pool cannot hold the candidates (block creation
 // undoes them).  Every thread of the CTA must call.
 __device__ __forceinline__ void order_body(const KParams &kp, int step)
 {
+    constexpr int W = 32;  // marks per thread and tile
     __shared__ int warp_sum[32];
     Ctrl *ctrl = kp.ctrl;
     const int par = step & 1;
@@ -978,40 +1111,99 @@ __device__ __forceinline__ void order_body(const KParams &kp, int step)
     if (ctrl->status || ncand <= 0 || n_old + ncand > kp.capacity) return;
     const int nb = kp.nbx * kp.nby * kp.nbz;
     const int T = blockDim.x, t = threadIdx.x;
-    const int chunk = (nb + T - 1) / T;
-    const int lo = min(nb, t * chunk), hi = min(nb, lo + chunk);
-    int cnt = 0;
-    for (int b = lo; b < hi; ++b) cnt += kp.cand_mark[b] == 1u;
-    // exclusive prefix of cnt over the CTA
-    const int lane = t & 31, warp = t >> 5;
-    int incl = cnt;
+    const int lane = t & 31, warp = t >> 5, nwarps = T >> 5;
+    int carry = 0;  // candidates in the tiles before this one
+    for (int base = 0; base < nb; base += T * W) {
+        const int lo = base + t * W;
+        uint32_t m = 0;
+        if (lo + W <= nb) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) warp_sum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < (T >> 5) ? warp_sum[lane] : 0;
+            for (int k = 0; k < W; ++k) m |= (uint32_t)(kp.cand_mark[lo + k] == 1u) << k;
+        } else {
+            for (int k = 0; lo + k < nb; ++k) m |= (uint32_t)(kp.cand_mark[lo + k] == 1u) << k;
+        }
+        const int cnt = __popc(m);
+        // exclusive prefix of cnt over the CTA
+        int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(FULL, w, o);
-            if (lane >= o) w += v;
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += v;
         }
-        warp_sum[lane] = w;  // inclusive over warps
-    }
-    __syncthreads();
-    int r = (warp ? warp_sum[warp - 1] : 0) + incl - cnt;
-    for (int b = lo; b < hi; ++b) {
-        if (kp.cand_mark[b] != 1u) continue;
-        kp.cand_list[r] = b;
-        kp.slot_of[b] = n_old + r;
-        ++r;
+        if (lane == 31) warp_sum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nwarps ? warp_sum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, w, o);
+                if (lane >= o) w += v;
+            }
+            warp_sum[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        int r = carry + (warp ? warp_sum[warp - 1] : 0) + incl - cnt;
+        carry += warp_sum[nwarps - 1];
+        while (m) {
+            const int b = lo + __ffs(m) - 1;
+            m &= m - 1u;
+            kp.cand_list[r] = b;
+            kp.slot_of[b] = n_old + r;
+            ++r;
+        }
+        __syncthreads();  // warp_sum is rewritten by the next tile
     }
 }
 
 __global__ void __launch_bounds__(1024) k_order(KParams kp) { order_body(kp, kp.ctrl->step); }
+
+// A-A: one cell of a block created in this step.  Its incoming
+// populations, as the A-B pull reads them (a meshed neighbour's value
+// towards it; the ambient equilibrium from unmeshed blocks, from blocks
+// created in this step and behind solid cells), sit for a source cell in a
+// meshed block at (source, opp(i)) after either kind of step: after a local
+// step that is where the source's post-collision value is; after a
+// neighbour step it is the value the source parked there for this block,
+// then unmeshed.  A local step reads them from the cell's own slots, so
+// they are copied there; in a neighbour step the new block's slots read as
+// the ambient equilibrium.  Then the cell's moments (as macro_cell, in pull
+// order) into mac.  wn: the block itself and the blocks created in this
+// step map to the ambient slot.  All lanes call.
+__device__ __forceinline__ void aa_new_cell(const KParams &kp, const WarpNbr &wn, float4 *mac, int slot,
+                                            int gid, int c, int lx, int ly, int lz, uint32_t bits,
+                                            int local)
+{
+    const bool nonsolid = !(bits & 1u);
+    const bool held = (bits >> HELD_BIT) & 1u;
+    float2 in[Q];
+    Unroll<0, Q>::run([&]<int I>() {
+        const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+        const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+        const uint32_t o = __shfl_sync(FULL, wn.fbase, k) + (uint32_t)(opp(I) * CELLS + lc);
+        const bool from_amb = ((bits >> I) & 1u) || held || !nonsolid;
+        in[I] = from_amb ? make_float2(kp.famb[0][I], kp.famb[1][I])
+                         : make_float2(__ldg(kp.f + o), __ldg(kp.f + o + Q * CELLS));
+    });
+    float *d = kp.f + (size_t)slot * kp.slot_floats + c;
+    float *hc = held ? kp.held_f + (size_t)kp.held_rank[gid] * kp.slot_floats + c : nullptr;
+    Moments m;
+    auto one = [&]<int I>() {
+        d[I * CELLS] = local ? in[I].x : kp.famb[0][I];
+        d[(Q + I) * CELLS] = local ? in[I].y : kp.famb[1][I];
+        if (hc) {
+            hc[I * CELLS] = kp.famb[0][I];
+            hc[(Q + I) * CELLS] = kp.famb[1][I];
+        }
+        m.template add<I>(0, in[I].x);
+        m.template add<I>(1, in[I].y);
+    };
+    one.template operator()<0>();
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        one.template operator()<pair_rep(P)>();
+        one.template operator()<opp(pair_rep(P))>();
+    });
+    if (nonsolid) mac[(size_t)slot * CELLS + c] = mac_pack(m.rho[0], psi_of(kp, m.rho[0]), m.rho[1]);
+}
 
 // Block creation (Sec. 4.2-4.3): the candidates found by k_macro get slots
 // after the meshed ones, start from the ambient resting equilibrium in both
@@ -1099,6 +1291,12 @@ __device__ __forceinline__ void activate_body(const KParams &kp, int step)
             atomicAdd(&ctrl->fluid_active, (unsigned long long)__popc(fluid));
         const WarpNbr wn = warp_nbr(kp, gid, slot, n_old, true);
         const float4 amb = mac_pack(kp.rho_amb[0], kp.psi_amb, kp.rho_amb[1]);
+        if constexpr (!S::DEV && NC == 2) {
+            if (kp.aa) {  // warp-uniform
+                aa_new_cell(kp, wn, mac, slot, gid, c, lx, ly, lz, bits, step & 1);
+                continue;
+            }
+        }
         if constexpr (!S::DEV) {
 #pragma unroll
             for (int a = 0; a < NC; ++a) {
@@ -1556,6 +1754,186 @@ __global__ void __launch_bounds__(THREADS) k_collide2(KParams kp)
     step_done(kp.ctrl, step);
 }
 
+// ---- A-A streaming: the two passes (FP32, two components) -------------------
+// As k_macro2 / k_collide2 with the A-A addressing above; the kind of step
+// (neighbour or local) follows the step count on the device, so captured
+// launches replay correctly.
+
+template <bool LOCAL>
+__device__ __forceinline__ void macro_aa_body(const KParams &kp, int step, int criterion)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (criterion && ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+        }
+        const bool live = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
+        Moments2 m;
+        pull2_aa<LOCAL>(kp, wn, slot, c, lx, ly, lz, bits, live, 0u,
+                        [&]<int I>(float2 v) { m.template add<I>(v); });
+        const float2 inv = make_float2(1.f / m.rho.x, 1.f / m.rho.y);
+        float u[2][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const float2 ud = mul2(m.j[d], inv);
+            u[0][d] = ud.x;
+            u[1][d] = ud.y;
+        }
+        kp.mac[(size_t)slot * CELLS + c] =
+            live ? mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (criterion) criterion_mark<2>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 4) k_macro_aa(KParams kp, int criterion)
+{
+    const int step = kp.ctrl->step;
+    if (step & 1)
+        macro_aa_body<true>(kp, step, criterion);
+    else
+        macro_aa_body<false>(kp, step, criterion);
+}
+
+// The collision writes every non-solid cell: fluid cells their new
+// populations, held cells their constants (the locations change from step
+// to step); in local steps solid cells also complete sectors, as in
+// k_collide2.  No lane leaves early: the write addresses of neighbour steps
+// come from shuffles.
+template <bool LOCAL, bool TAU1>
+__device__ __forceinline__ void collide_aa_body(const KParams &kp, int step)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (ctrl->status) return;
+    const int par = step & 1;
+    const int n_old = ctrl->n_active[par];
+    const int n = ctrl->n_active[par ^ 1];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 7)) return;
+    float *A = kp.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->cell_updates += (unsigned long long)n * CELLS;
+        ctrl->fluid_updates += ctrl->fluid_active;
+    }
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    uint32_t next_bits =
+        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const uint32_t bits = next_bits;
+        const int it2 = it + gridDim.x;
+        if (it2 < total) {
+            next_row = nbr_row_lane(kp, it2 / PARTS);
+            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+        }
+        const bool nonsolid = !(bits & 1u);
+        const bool held = (bits >> HELD_BIT) & 1u;
+        const bool live = nonsolid && !held;
+        // blocks created in this step: ambient sources of a local step
+        const unsigned fresh = LOCAL ? __ballot_sync(FULL, wn.slot >= n_old) : 0u;
+        const bool row_live = row_has(nonsolid);  // every lane takes part
+        const bool fill = LOCAL && (bits & 1u) && row_live;
+        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) continue;
+        Moments2 m;
+        float2 fin[TAU1 ? 1 : Q];
+        pull2_aa<LOCAL>(kp, wn, slot, c, lx, ly, lz, bits, nonsolid, fresh, [&]<int I>(float2 v) {
+            m.template add<I>(v);
+            if constexpr (!TAU1) fin[I] = v;
+        });
+        const float2 rho = m.rho;
+        const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+        float2 u[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
+        float2 F[3];
+        forces2<2>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
+        float2 v[3], nv[3], nu[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            v[d] = fma2(F[d], inv, u[d]);
+            nv[d] = sub2(make_float2(0.f, 0.f), v[d]);
+            nu[d] = sub2(make_float2(0.f, 0.f), u[d]);
+        }
+        const float2 one = splat(1.f);
+        const float2 cv = fma2(splat(-1.5f), fma2(v[0], v[0], fma2(v[1], v[1], mul2(v[2], v[2]))), one);
+        const float2 cu = fma2(splat(-1.5f), fma2(u[0], u[0], fma2(u[1], u[1], mul2(u[2], u[2]))), one);
+        float2 wrho[3];
+        Unroll<0, 3>::run([&]<int K>() {
+            constexpr int I = K == 0 ? 0 : (K == 1 ? 1 : 5);
+            wrho[K] = mul2(splat(wgt(I)), rho);
+        });
+        const float2 relax = splat(1.f - kp.omega);
+        float2 moving = make_float2(0.f, 0.f);
+        const uint32_t own = (uint32_t)slot * (uint32_t)kp.slot_floats + (uint32_t)c;
+        const bool store = nonsolid || fill;
+        const float *hc = kp.held_f;
+        if (held) hc += (size_t)kp.held_rank[kp.block_of[slot]] * kp.slot_floats + c;
+        // the 18 moving populations (Eqs. 10-12); the rest population from
+        // the mass balance sum_i f_i = rho (see k_collide)
+        Unroll<1, Q>::run([&]<int I>() {
+            const float2 ev = edot<I>(v, nv);
+            float2 f = mul2(wrho[wclass(I)], fma2(ev, fma2(ev, splat(4.5f), splat(3.f)), cv));
+            if constexpr (!TAU1) {
+                const float2 eu = edot<I>(u, nu);
+                const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
+                f = fma2(relax, sub2(fin[I], e0), f);
+            }
+            moving = add2(moving, f);
+            const uint32_t d = aa_dst<LOCAL, I>(wn, own, lx, ly, lz, bits);
+            if (store) {
+                A[d] = live ? f.x : (held ? __ldg(hc + I * CELLS) : 0.f);
+                A[d + Q * CELLS] = live ? f.y : (held ? __ldg(hc + (Q + I) * CELLS) : 0.f);
+            }
+        });
+        const float2 rest = sub2(rho, moving);
+        if (store) {
+            A[own] = live ? rest.x : (held ? __ldg(hc) : 0.f);
+            A[own + Q * CELLS] = live ? rest.y : (held ? __ldg(hc + Q * CELLS) : 0.f);
+        }
+        (void)cu;
+        if (live && kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+            float *up = kp.uprev + (size_t)slot * 2 * 3 * CELLS + c;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                up[d * CELLS] = u[d].x;
+                up[(3 + d) * CELLS] = u[d].y;
+            }
+        }
+    }
+}
+
+template <bool TAU1>
+__global__ void __launch_bounds__(THREADS, 3) k_collide_aa(KParams kp)
+{
+    const int step = *(volatile const int *)&kp.ctrl->step;
+    if (step & 1)
+        collide_aa_body<true, TAU1>(kp, step);
+    else
+        collide_aa_body<false, TAU1>(kp, step);
+    step_done(kp.ctrl, step);
+}
+
 // ---- TMA-staged step kernels (FP32, two components) -------------------------
 // One CTA of 512 threads per SM works on one block at a time: the block's
 // populations (both components, 77.8 KB, contiguous in the read buffer)
@@ -1979,8 +2357,8 @@ __global__ void __launch_bounds__(THREADS) k_output(KParams kp, int rdbuf, int c
             }
         }
         Moments m;
-        pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, ref,
-                     [&]<int I>(int a, float v) { m.template add<I>(a, v); });
+        pull_state<NC, ST>(kp, wn, rd, rdbuf, slot, c, lx, ly, lz, bits, live, ref,
+                           [&]<int I>(int a, float v) { m.template add<I>(a, v); });
         float rho[2] = {m.rho[0], m.rho[1]};
         float F[2][3];
         forces<NC>(kp, wn, moff, slot, c, lx, ly, lz, bits, live && !held, rho, F);
@@ -2037,6 +2415,26 @@ __device__ __forceinline__ void stored_cell(const KParams &kp, int rdbuf, int sl
             const float2 x = S::dec2(__ldg(src + i * CELLS));
             out[0][i] = live ? __fmaf_rn(wgt(i), rdst[0][i], x.x) : 0.f;
             out[1][i] = live ? __fmaf_rn(wgt(i), rdst[1][i], x.y) : 0.f;
+        }
+    } else if (kp.aa) {
+        // A-A: where the last step left each outgoing value (rdbuf is the
+        // parity of the next step; the initial state is laid out as after a
+        // local step)
+        const uint32_t own = (uint32_t)slot * (uint32_t)kp.slot_floats + (uint32_t)c;
+        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        if (rdbuf == 0) {
+            Unroll<0, Q>::run([&]<int I>() {
+                const uint32_t d = aa_dst<true, I>(WarpNbr{}, own, lx, ly, lz, bits);
+                out[0][I] = live ? __ldg(kp.f + d) : 0.f;
+                out[1][I] = live ? __ldg(kp.f + d + Q * CELLS) : 0.f;
+            });
+        } else {
+            const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
+            Unroll<0, Q>::run([&]<int I>() {
+                const uint32_t d = aa_dst<false, I>(wn, own, lx, ly, lz, bits);
+                out[0][I] = live ? __ldg(kp.f + d) : 0.f;
+                out[1][I] = live ? __ldg(kp.f + d + Q * CELLS) : 0.f;
+            });
         }
     } else {
         for (int a = 0; a < kp.ncomp; ++a)
@@ -2138,8 +2536,8 @@ __global__ void __launch_bounds__(THREADS) k_features(KParams kp, int par, const
                         ref[1] = m.y;
                     }
                     Moments m;
-                    pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, use, false, ref,
-                                 [&]<int I>(int a, float f) { m.template add<I>(a, f); });
+                    pull_state<NC, ST>(kp, wn, rd, par, slot, c, lx, ly, lz, bits, use, ref,
+                                       [&]<int I>(int a, float f) { m.template add<I>(a, f); });
                     if (use) {
                         r0 += m.rho[0];
                         r1 += NC == 2 ? m.rho[1] : 0.f;
@@ -2339,6 +2737,7 @@ struct Launch {
             if (kp.ncomp == 2) return launch_persistent<k_macro_dev<2, ST>>(sms, s, kp, criterion);
             return launch_persistent<k_macro_dev<1, ST>>(sms, s, kp, criterion);
         } else {
+            if (kp.aa) return launch_persistent<k_macro_aa>(sms, s, kp, criterion);
             if (kp.ncomp == 2 && kp.staged) return launch_staged<k_macro2_staged>(sms, s, kp, criterion);
             if (kp.ncomp == 2) return launch_persistent<k_macro2>(sms, s, kp, criterion);
             return launch_persistent<k_macro<1>>(sms, s, kp, criterion);
@@ -2365,6 +2764,10 @@ struct Launch {
             if (tau1) return launch_persistent<k_collide_dev<1, true, ST>>(sms, s, kp);
             return launch_persistent<k_collide_dev<1, false, ST>>(sms, s, kp);
         } else {
+            if (kp.aa) {
+                if (tau1) return launch_persistent<k_collide_aa<true>>(sms, s, kp);
+                return launch_persistent<k_collide_aa<false>>(sms, s, kp);
+            }
             if (kp.ncomp == 2 && kp.staged) {
                 if (tau1) return launch_staged<k_collide2_staged<true>>(sms, s, kp);
                 return launch_staged<k_collide2_staged<false>>(sms, s, kp);

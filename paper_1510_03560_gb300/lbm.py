@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm_checked.so" if os.environ.get("LBM_CHECKED
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, 1, 2, 3, 4, 5
 EXEC = {"stream": 0, "graph": 1, "persistent": 2, "staged": 3}  # LBM_EXEC_*
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}  # LBM_STORAGE_*
+STREAMING = {"ab": 0, "aa": 1}  # LBM_STREAM_*
 Q = 19
 EDGE = 8
 
@@ -34,6 +35,7 @@ class Params(C.Structure):
         ("periodic", C.c_int * 3),
         ("progressive", C.c_int),
         ("storage", C.c_int),
+        ("streaming", C.c_int),
         ("tau", C.c_double), ("beta", C.c_double),
         ("pr_a", C.c_double), ("pr_b", C.c_double), ("pr_R", C.c_double), ("pr_omega", C.c_double),
         ("T_over_Tc", C.c_double),
@@ -182,6 +184,7 @@ class LBM:
 
     Keyword parameters mirror lbm_params: nx, ny, nz, ncomp, periodic,
     progressive, storage ("fp32", "fp16", "bf16" or the LBM_STORAGE_* code),
+    streaming ("ab" or "aa", the LBM_STREAM_* pattern),
     tau, beta, pr_a, pr_b, pr_R, pr_omega, T_over_Tc, g_self, g_cross, g_ads,
     grav, rho_ref, S, max_blocks.  ``stream``: a
     torch.cuda.Stream (default: the current stream).  ``torch_alloc``:
@@ -209,6 +212,9 @@ class LBM:
         st = kw.get("storage", 0)
         p.storage = STORAGE[st] if isinstance(st, str) else int(st)
         self.storage = p.storage
+        sp = kw.get("streaming", 0)
+        p.streaming = STREAMING[sp] if isinstance(sp, str) else int(sp)
+        self.streaming = p.streaming
         p.tau = float(kw.get("tau", 1.0))
         p.beta = float(kw.get("beta", 1.16))
         p.pr_a = float(kw.get("pr_a", 2.0 / 49.0))

@@ -82,6 +82,9 @@ def _params(**over):
     (dict(max_blocks=-2), "max_blocks"),
     (dict(storage=3), "storage form"),
     (dict(storage=-1), "storage form"),
+    (dict(streaming=2), "streaming pattern"),
+    (dict(streaming=1, storage=1), "A-A streaming needs"),
+    (dict(streaming=1, ncomp=1), "A-A streaming needs"),
 ])
 def test_create_rejects_bad_parameters_without_cuda(lib, over, frag):
     h = C.c_void_p()
