@@ -280,9 +280,10 @@ cudaEvent_t take_event(lbm_ctx *c)
     return e;
 }
 
-// Launch `fn` with optional timing events around it.
+// Launch `fn` (`kernels` kernel launches) with optional timing events
+// around it.
 template <class F>
-cudaError_t timed(lbm_ctx *c, int kind, F &&fn)
+cudaError_t timed(lbm_ctx *c, int kind, F &&fn, int kernels = 1)
 {
     Event ev{kind, nullptr, nullptr};
     if (c->profiling) {
@@ -291,7 +292,7 @@ cudaError_t timed(lbm_ctx *c, int kind, F &&fn)
         if (ev.a) cudaEventRecord(ev.a, c->stream);
     }
     cudaError_t e = fn();
-    c->launches += 1;
+    c->launches += kernels;
     if (c->profiling && ev.a && ev.b) {
         cudaEventRecord(ev.b, c->stream);
         c->pending.push_back(ev);
@@ -392,7 +393,8 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
             int rc = ensure_graph(c);
             if (rc) return rc;
             for (int p = 0; p < chunk / 2; ++p)
-                CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return cudaGraphLaunch(c->gexec, c->stream); }));
+                CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return cudaGraphLaunch(c->gexec, c->stream); },
+                                      2 * (c->p.progressive ? 4 : 2)));
             k += 2 * (chunk / 2);
             continue;
         }
@@ -401,7 +403,8 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
                      }));
         if (c->p.progressive)
             CUDA_OR_FAIL(c, timed(c, K_ACTIVATE,
-                                  [&] { return launch_activate(c->kp, t, c->sms, c->stream); }));
+                                  [&] { return launch_activate(c->kp, t, c->sms, c->stream); },
+                                  2));  // k_order + k_activate
         CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, c->sms, c->stream); }));
         k += 1;
     }

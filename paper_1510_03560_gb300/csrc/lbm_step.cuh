@@ -1094,7 +1094,8 @@ __global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KPara
 // criterion marks candidates in any order (cand_mark 1, a provisional slot);
 // here they are renumbered in ascending block order, slot n_old + rank, by
 // a prefix scan over the marks.  The marks go in tiles of 32 per thread: a
-// thread loads its 32 consecutive marks at once into a bit mask, a
+// thread gets its 32 consecutive marks as a bit mask (warp ballots over
+// coalesced rows), a
 // warp-shuffle scan and a scan of the warp totals give its first rank, and
 // the candidates are written from the mask; a running total carries the
 // ranks from tile to tile.  Block creation then sets the mark to 2 (meshed).
@@ -1115,12 +1116,15 @@ __device__ __forceinline__ void order_body(const KParams &kp, int step)
     int carry = 0;  // candidates in the tiles before this one
     for (int base = 0; base < nb; base += T * W) {
         const int lo = base + t * W;
+        // a warp reads its 32 x 32 marks one coalesced row at a time; lane k
+        // keeps the ballot of row k, i.e. the marks lo .. lo + 31 of its own
+        const int wbase = base + warp * 32 * W;
         uint32_t m = 0;
-        if (lo + W <= nb) {
 #pragma unroll
-            for (int k = 0; k < W; ++k) m |= (uint32_t)(kp.cand_mark[lo + k] == 1u) << k;
-        } else {
-            for (int k = 0; lo + k < nb; ++k) m |= (uint32_t)(kp.cand_mark[lo + k] == 1u) << k;
+        for (int k = 0; k < W; ++k) {
+            const int b = wbase + k * 32 + lane;
+            const unsigned row = __ballot_sync(FULL, b < nb && kp.cand_mark[b] == 1u);
+            if (lane == k) m = row;
         }
         const int cnt = __popc(m);
         // exclusive prefix of cnt over the CTA
