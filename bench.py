@@ -144,9 +144,10 @@ WORKLOADS = {
 }
 
 
-def make_case(S=None, size=256, workload="injection"):
+def make_case(S=None, size=256, workload="injection", block="8x8x8"):
     from paper_1510_03560_gb300 import workloads as W
     kw = {} if S is None else {"S": S}
+    kw["block"] = tuple(int(v) for v in block.split("x"))
     if workload in WORKLOADS:
         kw.update(WORKLOADS[workload][1])
     elif size != 256:
@@ -273,7 +274,8 @@ def run_batch(args):
     from paper_1510_03560_gb300 import lbm as L
     uuid = device_uuid(torch, 0)
     cases = BT.c3_cases(64)
-    batch, place = BT.pack(cases)
+    shape, shape_rates = BT.autotune_shape(L, cases, steps=20)
+    batch, place = BT.pack(cases, block=shape)
     best, tune_ms = BT.autotune(L, batch, steps=20)
 
     def timed(case, mode, steps, warmup):
@@ -313,7 +315,10 @@ def run_batch(args):
         "config": {
             "workload": "batch of 64 seeded simulations (droplet impact or porous injection, "
                         "grids drawn from multiples of 16 in [32, 128]) in one shared block pool",
-            "grid": [batch["params"][k] for k in ("nx", "ny", "nz")], "block": [8, 8, 8],
+            "grid": [batch["params"][k] for k in ("nx", "ny", "nz")], "block": list(shape),
+            "block_autotuned_20_steps": {"x".join(map(str, k)): {"ms_per_step": round(v["ms_per_step"], 4),
+                                                                 "mlups": round(v["mlups"], 1)}
+                                         for k, v in shape_rates.items()},
             "pool_blocks": batch["params"]["max_blocks"], "exec_autotuned": best,
             "autotune_ms_20_steps": {k: round(v, 3) for k, v in tune_ms.items()},
             "modes": modes,
@@ -377,6 +382,8 @@ def main():
                          "quoted on")
     ap.add_argument("--exec", default="stream", choices=["stream", "graph", "persistent", "staged"],
                     help="how the library enqueues the steps")
+    ap.add_argument("--block", default="8x8x8", choices=["8x8x8", "16x8x4", "16x4x8", "32x4x4"],
+                    help="cells per block along x, y, z")
     ap.add_argument("--streaming", default="ab", choices=["ab", "aa"],
                     help="population streaming pattern: two arrays (A-B) or one updated in place (A-A)")
     ap.add_argument("--no-forms", action="store_true",
@@ -400,7 +407,7 @@ def main():
         dist.barrier()
     from paper_1510_03560_gb300 import lbm as L
     uuid = device_uuid(torch, local)
-    case = make_case(args.S, args.size, args.workload)
+    case = make_case(args.S, args.size, args.workload, args.block)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     if args.static_only:
         st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage,
@@ -490,8 +497,10 @@ def main():
              for name, v in zip(("macro", "activate", "collide", "other"), prog["kernel_ms"])}
     config = {
         "workload": (WORKLOADS[args.workload][0] if args.workload in WORKLOADS
-                     else WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}"),
-        "mode": "progressive", "grid": [case["params"][k] for k in ("nx", "ny", "nz")], "block": [8, 8, 8],
+                     else WORKLOAD if args.size == 256 else f"{args.size}^3 variant of: {WORKLOAD}"
+                     ).replace("8^3 blocks", "8^3 blocks" if args.block == "8x8x8" else f"{args.block} blocks"),
+        "mode": "progressive", "grid": [case["params"][k] for k in ("nx", "ny", "nz")],
+        "block": list(case["params"]["block"]),
         "storage": args.storage, "exec": args.exec, "streaming": args.streaming,
         "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),

@@ -98,7 +98,7 @@ typedef void *(*lbm_alloc_fn)(size_t bytes, void *user);
 typedef void (*lbm_free_fn)(void *ptr, void *user);
 
 typedef struct lbm_params {
-    int nx, ny, nz;      /* grid, each a positive multiple of 8 */
+    int nx, ny, nz;      /* grid, each a positive multiple of the block extent */
     int ncomp;           /* 1 or 2; component 0 follows the Peng-Robinson EOS,
                             component 1 is an ideal gas (p = rho / 3, psi = 0) */
     int periodic[3];     /* per axis: 1 wraps around, 0 ends in solid cells */
@@ -106,6 +106,10 @@ typedef struct lbm_params {
                             block holding a non-solid cell meshed from the start */
     int storage;         /* LBM_STORAGE_FP32 (0), _FP16 or _BF16 */
     int streaming;       /* LBM_STREAM_AB (0) or LBM_STREAM_AA */
+    int block[3];        /* cells per block along x, y, z (the paper's sub-domain
+                            shape, Sec. 4.1): 8x8x8 (default; {0, 0, 0} selects it),
+                            16x8x4, 16x4x8 or 32x4x4.  Shapes other than 8^3 need the
+                            FP32 storage form and no activation proposer. */
     double tau;          /* BGK relaxation time, Eq. 1 (> 0.5) */
     double beta;         /* weighting term of Eq. 8 (the paper uses 1.16) */
     double pr_a, pr_b, pr_R, pr_omega; /* Peng-Robinson a, b, R, acentric factor, Eq. 7 */
@@ -347,7 +351,8 @@ int lbm_mlp_adam(lbm_mlp *mlp, float lr, float beta1, float beta2, float eps, in
 /* Use `mlp` (not owned; NULL turns the proposer off) every `period` steps
  * of lbm_step / lbm_step_async: frontier blocks whose probability (BF16
  * inference) exceeds `threshold` are prepared on a side stream.  The mlp
- * must outlive its use by the context.  Progressive mode only. */
+ * must outlive its use by the context.  Progressive mode and 8x8x8 blocks
+ * only (LBM_EINVAL otherwise). */
 int lbm_set_proposer(lbm_ctx *ctx, lbm_mlp *mlp, int period, float threshold);
 
 #ifdef __cplusplus

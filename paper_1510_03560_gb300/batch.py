@@ -13,7 +13,9 @@ of the simulations' non-solid blocks).  The simulations must share the
 physics and the ambient state.
 
 The execution mode (lbm_set_exec) that suits a batch is chosen by
-`autotune`, which times each mode on a scratch context.
+`autotune`, which times each mode on a scratch context; the block shape by
+`autotune_shape`, which packs and times the batch once per shape that tiles
+every member.
 """
 from __future__ import annotations
 
@@ -23,8 +25,7 @@ import numpy as np
 
 from . import workloads as W
 
-EDGE = 8
-GAP = EDGE  # one all-solid block between simulations
+EDGE = 8     # the default block, 8 x 8 x 8 cells
 SIZES = tuple(range(32, 129, 16))
 
 
@@ -49,7 +50,7 @@ def c3_cases(count: int = 64, seed0: int = 1510035700):
 
 
 def _shared_params(cases):
-    keys = set().union(*(c["params"].keys() for c in cases)) - {"nx", "ny", "nz", "max_blocks"}
+    keys = set().union(*(c["params"].keys() for c in cases)) - {"nx", "ny", "nz", "max_blocks", "block"}
     p0 = cases[0]["params"]
     for c in cases[1:]:
         for k in keys:
@@ -62,34 +63,41 @@ def _shared_params(cases):
     return {k: p0[k] for k in keys if k in p0}
 
 
-def nonsolid_blocks(cell_type) -> int:
+def nonsolid_blocks(cell_type, block=(EDGE, EDGE, EDGE)) -> int:
     nz, ny, nx = cell_type.shape
-    b = (cell_type != W.SOLID).reshape(nz // EDGE, EDGE, ny // EDGE, EDGE, nx // EDGE, EDGE)
+    bx, by, bz = block
+    b = (cell_type != W.SOLID).reshape(nz // bz, bz, ny // by, by, nx // bx, bx)
     return int(b.any(axis=(1, 3, 5)).sum())
 
 
-def pack(cases, width: int | None = None):
+def tiles(cases, block) -> bool:
+    """Whether every simulation's size is a multiple of the block."""
+    return all(c["params"][k] % b == 0 for c in cases for k, b in zip(("nx", "ny", "nz"), block))
+
+
+def pack(cases, width: int | None = None, block=(EDGE, EDGE, EDGE)):
     """One case holding every simulation: shelf packing in x-y (rows of the
-    given width, tallest first), one layer in z.  Returns (case, placements),
-    placements[k] = (x0, y0, z0, nx, ny, nz) of simulation k."""
+    given width, tallest first), one layer in z, one all-solid block between
+    neighbours.  Returns (case, placements), placements[k] = (x0, y0, z0,
+    nx, ny, nz) of simulation k."""
     shared = _shared_params(cases)
+    bx, by, _ = block
     dims = [(c["params"]["nx"], c["params"]["ny"], c["params"]["nz"]) for c in cases]
-    for d in dims:
-        if any(v % EDGE for v in d):
-            raise ValueError("simulation sizes must be multiples of 8")
+    if not tiles(cases, block):
+        raise ValueError(f"simulation sizes must be multiples of the {block} block")
     if width is None:
-        area = sum((d[0] + GAP) * (d[1] + GAP) for d in dims)
-        width = max(max(d[0] for d in dims), int(math.ceil(math.sqrt(area) / EDGE)) * EDGE)
+        area = sum((d[0] + bx) * (d[1] + by) for d in dims)
+        width = max(max(d[0] for d in dims), int(math.ceil(math.sqrt(area) / bx)) * bx)
     order = sorted(range(len(cases)), key=lambda i: (-dims[i][1], -dims[i][0], i))
     place = [None] * len(cases)
     x = y = row_h = 0
     for i in order:
         nx, ny, nz = dims[i]
         if x > 0 and x + nx > width:
-            y += row_h + GAP
+            y += row_h + by
             x = row_h = 0
         place[i] = (x, y, 0, nx, ny, nz)
-        x += nx + GAP
+        x += nx + bx
         row_h = max(row_h, ny)
     NX = max(p[0] + p[3] for p in place)
     NY = max(p[1] + p[4] for p in place)
@@ -106,8 +114,8 @@ def pack(cases, width: int | None = None):
         rho[(slice(None),) + sl] = c["rho_init"]
         if c["u_init"] is not None:
             u[(slice(None), slice(None)) + sl] = c["u_init"]
-    params = dict(shared, nx=NX, ny=NY, nz=NZ,
-                  max_blocks=sum(nonsolid_blocks(c["cell_type"]) for c in cases))
+    params = dict(shared, nx=NX, ny=NY, nz=NZ, block=tuple(block),
+                  max_blocks=sum(nonsolid_blocks(c["cell_type"], block) for c in cases))
     batch = dict(cell_type=ct, rho_init=rho, u_init=u, rho_amb=cases[0]["rho_amb"].copy(),
                  params=params)
     return batch, place
@@ -121,11 +129,12 @@ def split(field, placements):
 
 def block_map(batch_params, placements, k):
     """Batch block id of every block of simulation k, [nbz][nby][nbx]."""
-    NBX, NBY = batch_params["nx"] // EDGE, batch_params["ny"] // EDGE
+    ex, ey, ez = batch_params.get("block", (EDGE, EDGE, EDGE))
+    NBX, NBY = batch_params["nx"] // ex, batch_params["ny"] // ey
     x0, y0, z0, nx, ny, nz = placements[k]
-    bz, by, bx = np.meshgrid(np.arange(nz // EDGE), np.arange(ny // EDGE), np.arange(nx // EDGE),
+    bz, by, bx = np.meshgrid(np.arange(nz // ez), np.arange(ny // ey), np.arange(nx // ex),
                              indexing="ij")
-    return (x0 // EDGE + bx) + NBX * ((y0 // EDGE + by) + NBY * (z0 // EDGE + bz))
+    return (x0 // ex + bx) + NBX * ((y0 // ey + by) + NBY * (z0 // ez + bz))
 
 
 def autotune(L, case, steps: int = 40, modes=("stream", "graph", "persistent", "staged"), storage="fp32"):
@@ -148,3 +157,35 @@ def autotune(L, case, steps: int = 40, modes=("stream", "graph", "persistent", "
         times[m] = a.elapsed_time(b)
         sim.close()
     return min(times, key=times.get), times
+
+
+def autotune_shape(L, cases, shapes=None, steps: int = 40, warmup: int = 4, exec_mode="stream"):
+    """Pack the simulations once per block shape that tiles all of them
+    (default: every shape of the library), time `steps` steps after
+    `warmup` (CUDA events on the library's stream) and return (the shape
+    with the least time per step, {shape: {"ms_per_step", "mlups"}}).  The
+    time decides, not the cell-update rate: a coarser shape meshes more
+    cells for the same simulations."""
+    import torch
+    res = {}
+    for shape in shapes or L.SHAPES:
+        if not tiles(cases, shape):
+            continue
+        batch, _ = pack(cases, block=shape)
+        sim = L.from_case(batch)
+        sim.set_exec(exec_mode)
+        sim.step(warmup)
+        st0 = sim.stats()
+        stream = sim.torch_stream
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step_async(steps)
+        b.record(stream)
+        sim.sync()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        cells = sim.stats()["cell_updates"] - st0["cell_updates"]
+        res[tuple(shape)] = {"ms_per_step": ms / steps, "mlups": cells / (ms * 1e-3) / 1e6}
+        sim.close()
+    return min(res, key=lambda k: res[k]["ms_per_step"]), res

@@ -12,8 +12,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm.so")
-SOURCES = ["lbm_kernels.cu", "lbm_kernels_f16.cu", "lbm_kernels_bf16.cu", "lbm_capi.cpp",
-           "lbm_noalloc.cu", "lbm_mlp.cu"]
+SOURCES = ["lbm_kernels.cu", "lbm_kernels_f16.cu", "lbm_kernels_bf16.cu", "lbm_kernels_16x8x4.cu",
+           "lbm_kernels_16x4x8.cu", "lbm_kernels_32x4x4.cu", "lbm_capi.cpp", "lbm_noalloc.cu", "lbm_mlp.cu"]
 HEADERS = [os.path.join(CSRC, "lbm_internal.h"), os.path.join(CSRC, "lbm_step.cuh"),
            os.path.join(ROOT, "include", "lbm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

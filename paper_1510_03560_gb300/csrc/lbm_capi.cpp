@@ -46,6 +46,7 @@ struct lbm_ctx {
     int sms = 1;
     int ctas_per_sm = 1;
     int nbx = 0, nby = 0, nbz = 0;
+    int bx = EDGE, by = EDGE, bz = EDGE;  // cells per block along x, y, z
     long long nblocks = 0;
     int capacity = 0;
     bool geometry = false;
@@ -182,12 +183,35 @@ void release(lbm_ctx *c, void *ptr)
         }
 }
 
+// Cell index inside its block: x + bx (y + by z) in block-local coordinates.
+int local_cell(const lbm_ctx *c, int x, int y, int z)
+{
+    return (x % c->bx) + c->bx * ((y % c->by) + c->by * (z % c->bz));
+}
+
+// Index of the block shape p asks for in BLOCK_SHAPES ({0, 0, 0}: the
+// default), or -1.
+int shape_index(const lbm_params *p)
+{
+    if (p->block[0] == 0 && p->block[1] == 0 && p->block[2] == 0) return 0;
+    for (int i = 0; i < NSHAPES; ++i)
+        if (p->block[0] == BLOCK_SHAPES[i].x && p->block[1] == BLOCK_SHAPES[i].y &&
+            p->block[2] == BLOCK_SHAPES[i].z)
+            return i;
+    return -1;
+}
+
 int validate(const lbm_params *p)
 {
     if (!p) return fail(nullptr, LBM_EINVAL, "params is NULL");
-    if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || p->nx % EDGE || p->ny % EDGE || p->nz % EDGE)
-        return fail(nullptr, LBM_EINVAL, "grid %dx%dx%d is not a positive multiple of %d", p->nx,
-                    p->ny, p->nz, EDGE);
+    const int si = shape_index(p);
+    if (si < 0)
+        return fail(nullptr, LBM_EINVAL, "unsupported block shape %dx%dx%d (8x8x8, 16x8x4, 16x4x8, 32x4x4)",
+                    p->block[0], p->block[1], p->block[2]);
+    const BlockShape sh = BLOCK_SHAPES[si];
+    if (p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || p->nx % sh.x || p->ny % sh.y || p->nz % sh.z)
+        return fail(nullptr, LBM_EINVAL, "grid %dx%dx%d is not a positive multiple of the %dx%dx%d block",
+                    p->nx, p->ny, p->nz, sh.x, sh.y, sh.z);
     if (p->ncomp != 1 && p->ncomp != 2)
         return fail(nullptr, LBM_EINVAL, "ncomp must be 1 or 2, got %d", p->ncomp);
     if (!(p->tau > 0.5) || !std::isfinite(p->tau))
@@ -202,6 +226,8 @@ int validate(const lbm_params *p)
         return fail(nullptr, LBM_EINVAL, "unknown streaming pattern %d", p->streaming);
     if (p->streaming == LBM_STREAM_AA && (p->storage != LBM_STORAGE_FP32 || p->ncomp != 2))
         return fail(nullptr, LBM_EINVAL, "A-A streaming needs the FP32 storage form and two components");
+    if (si != 0 && p->storage != LBM_STORAGE_FP32)
+        return fail(nullptr, LBM_EINVAL, "block shapes other than 8x8x8 need the FP32 storage form");
     if ((p->dev_alloc == nullptr) != (p->dev_free == nullptr))
         return fail(nullptr, LBM_EINVAL, "dev_alloc and dev_free must be given together");
     for (int a = 0; a < 3; ++a)
@@ -210,7 +236,7 @@ int validate(const lbm_params *p)
     if (p->g_self != 0.0 && (p->pr_b <= 0.0 || p->pr_a <= 0.0 || p->pr_R <= 0.0 ||
                              p->T_over_Tc <= 0.0))
         return fail(nullptr, LBM_EINVAL, "Peng-Robinson a, b, R and T/Tc must be > 0");
-    long long nb = (long long)(p->nx / EDGE) * (p->ny / EDGE) * (p->nz / EDGE);
+    long long nb = (long long)(p->nx / sh.x) * (p->ny / sh.y) * (p->nz / sh.z);
     if (nb > INT32_MAX / 2) return fail(nullptr, LBM_EINVAL, "grid too large");
     return LBM_OK;
 }
@@ -227,6 +253,7 @@ void fill_physics(lbm_ctx *c)
     k.capacity = c->capacity;
     k.progressive = p.progressive ? 1 : 0;
     k.storage = p.storage;
+    k.shape = shape_index(&p);
     k.omega = (float)(1.0 / p.tau);
     k.beta = (float)p.beta;
     k.g_self = (float)p.g_self;
@@ -466,9 +493,13 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
     if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
     c->p = *p;
     c->stream = (cudaStream_t)p->stream;
-    c->nbx = p->nx / EDGE;
-    c->nby = p->ny / EDGE;
-    c->nbz = p->nz / EDGE;
+    const BlockShape sh = BLOCK_SHAPES[shape_index(p)];
+    c->bx = sh.x;
+    c->by = sh.y;
+    c->bz = sh.z;
+    c->nbx = p->nx / sh.x;
+    c->nby = p->ny / sh.y;
+    c->nbz = p->nz / sh.z;
     c->nblocks = (long long)c->nbx * c->nby * c->nbz;
     long long cap = p->max_blocks > 0 ? std::min<long long>(p->max_blocks, c->nblocks) : c->nblocks;
     c->capacity = (int)cap;
@@ -601,8 +632,8 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
         for (int y = 0; y < p.ny; ++y)
             for (int x = 0; x < p.nx; ++x) {
                 const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
-                const long long b = (x / EDGE) + c->nbx * ((long long)(y / EDGE) + (long long)c->nby * (z / EDGE));
-                const int lc = (x & 7) | ((y & 7) << 3) | ((z & 7) << 6);
+                const long long b = (x / c->bx) + c->nbx * ((long long)(y / c->by) + (long long)c->nby * (z / c->bz));
+                const int lc = local_cell(c, x, y, z);
                 if (cell_type[i] == LBM_CELL_SOLID) {
                     c->solid_h[b * MASK_WORDS + (lc >> 5)] |= 1u << (lc & 31);
                     continue;
@@ -725,8 +756,8 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
             for (int a = 0; a < nc; ++a) {
                 float *dst = host.data() + ((size_t)r * nc + a) * 4 * CELLS;
                 for (int lc = 0; lc < CELLS; ++lc) {
-                    const int x = bx * EDGE + (lc & 7), y = by * EDGE + ((lc >> 3) & 7),
-                              z = bz * EDGE + (lc >> 6);
+                    const int x = bx * c->bx + lc % c->bx, y = by * c->by + (lc / c->bx) % c->by,
+                              z = bz * c->bz + lc / (c->bx * c->by);
                     const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
                     dst[lc] = rho_init[a * ncell + i];
                     for (int d = 0; d < 3; ++d)
@@ -789,7 +820,8 @@ int lbm_get_macro(lbm_ctx *c, int comp, float *rho, float *ux, float *uy, float 
         const int bx = (int)(b % c->nbx), by = (int)((b / c->nbx) % c->nby),
                   bz = (int)(b / ((long long)c->nbx * c->nby));
         for (int lc = 0; lc < CELLS; ++lc) {
-            const int x = bx * EDGE + (lc & 7), y = by * EDGE + ((lc >> 3) & 7), z = bz * EDGE + (lc >> 6);
+            const int x = bx * c->bx + lc % c->bx, y = by * c->by + (lc / c->bx) % c->by,
+                      z = bz * c->bz + lc / (c->bx * c->by);
             const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
             const bool sol = (c->solid_h[b * MASK_WORDS + (lc >> 5)] >> (lc & 31)) & 1u;
             if (rho) rho[i] = sol ? 0.f : c->rho_amb[comp];
@@ -821,7 +853,8 @@ int lbm_get_macro(lbm_ctx *c, int comp, float *rho, float *ux, float *uy, float 
             const int b = block_of[s0 + r];
             const int bx = b % c->nbx, by = (b / c->nbx) % c->nby, bz = b / (c->nbx * c->nby);
             for (int lc = 0; lc < CELLS; ++lc) {
-                const int x = bx * EDGE + (lc & 7), y = by * EDGE + ((lc >> 3) & 7), z = bz * EDGE + (lc >> 6);
+                const int x = bx * c->bx + lc % c->bx, y = by * c->by + (lc / c->bx) % c->by,
+                      z = bz * c->bz + lc / (c->bx * c->by);
                 const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
                 for (int q = 0; q < 4; ++q)
                     if (outs[q]) outs[q][i] = host[((size_t)r * 4 + q) * CELLS + lc];
@@ -981,6 +1014,7 @@ int lbm_frontier_features(lbm_ctx *c, int32_t *blocks, float *feat, long long ca
     if (!c || !n) return LBM_EINVAL;
     if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
     if (cap > 0 && (!blocks || !feat)) return fail(c, LBM_EINVAL, "blocks and feat are required");
+    if (c->kp.shape != 0) return fail(c, LBM_EINVAL, "frontier features are defined for 8x8x8 blocks");
     DeviceGuard g(c->device);
     int rc = ensure_frontier_buffers(c);
     if (rc) return rc;
@@ -1030,6 +1064,7 @@ int lbm_activation_steps(lbm_ctx *c, int32_t *out)
 int lbm_set_proposer(lbm_ctx *c, lbm_mlp *mlp, int period, float threshold)
 {
     if (!c) return LBM_EINVAL;
+    if (mlp && c->kp.shape != 0) return fail(c, LBM_EINVAL, "the activation proposer needs 8x8x8 blocks");
     DeviceGuard g(c->device);
     drop_graph(c);
     if (!mlp) {

@@ -9,7 +9,15 @@
 
 namespace lbm {
 
-constexpr int EDGE = 8;     // cells per block edge
+constexpr int EDGE = 8;     // cells per block edge of the default 8^3 shape
+
+// Block shapes the step kernels are compiled for (cells along x, y, z; 512
+// cells each, x-rows of whole 32-byte sectors).  Index 0 is the default.
+struct BlockShape {
+    int x, y, z;
+};
+constexpr int NSHAPES = 4;
+constexpr BlockShape BLOCK_SHAPES[NSHAPES] = {{8, 8, 8}, {16, 8, 4}, {16, 4, 8}, {32, 4, 4}};
 constexpr int CELLS = 512;  // cells per block
 constexpr int Q = 19;       // D3Q19
 constexpr int MASK_WORDS = CELLS / 32;
@@ -96,6 +104,8 @@ struct KParams {
                         // Q * CELLS (16-bit forms)
     long long barrier_spins;  // bounded wait of a grid barrier or a bulk copy (polls)
     int staged;         // FP32, two components: TMA-staged pass kernels
+    int shape;          // index into BLOCK_SHAPES (the FP32 form has all;
+                        // the 16-bit forms only 8^3)
     // A-A streaming (FP32, two components): one population array (f, with
     // buf_stride 0, so that both parities address it), updated in place
     int aa;
@@ -125,6 +135,9 @@ struct StorageOps {
     cudaError_t (*run)(const KParams &, int, int, int, cudaStream_t);
 };
 const StorageOps *storage_ops_fp32();
+const StorageOps *storage_ops_fp32_16x8x4();
+const StorageOps *storage_ops_fp32_16x4x8();
+const StorageOps *storage_ops_fp32_32x4x4();
 const StorageOps *storage_ops_fp16();
 const StorageOps *storage_ops_bf16();
 

@@ -88,7 +88,13 @@ const StorageOps &ops_of(const KParams &kp)
     switch (kp.storage) {
     case LBM_STORAGE_FP16: return *storage_ops_fp16();
     case LBM_STORAGE_BF16: return *storage_ops_bf16();
-    default: return *storage_ops_fp32();
+    default:
+        switch (kp.shape) {
+        case 1: return *storage_ops_fp32_16x8x4();
+        case 2: return *storage_ops_fp32_16x4x8();
+        case 3: return *storage_ops_fp32_32x4x4();
+        default: return *storage_ops_fp32();
+        }
     }
 }
 

@@ -213,12 +213,35 @@ __device__ __forceinline__ typename Store<ST>::T *pops(const KParams &kp)
         return reinterpret_cast<uint32_t *>(kp.h);
 }
 
-// Neighbour-block index (0..26) of a local coordinate in [-1, 8].
-__device__ __forceinline__ int side(int v) { return v < 0 ? 0 : (v > 7 ? 2 : 1); }
-__device__ __forceinline__ int nbk(int x, int y, int z) { return side(x) + 3 * side(y) + 9 * side(z); }
+// ---- block shape -------------------------------------------------------------
+// BX x BY x BZ cells per block (512 in all), cell c = x + BX (y + BY z).  The
+// default is 8^3; a translation unit may define LBM_BLOCK_X/Y/Z before
+// including this file to compile the kernels for another shape.  x-rows are
+// whole 32-byte sectors (BX a multiple of 8), so a warp (32 consecutive
+// cells) still reads and writes whole sectors.
+#ifndef LBM_BLOCK_X
+#define LBM_BLOCK_X 8
+#define LBM_BLOCK_Y 8
+#define LBM_BLOCK_Z 8
+#endif
+constexpr int BX = LBM_BLOCK_X, BY = LBM_BLOCK_Y, BZ = LBM_BLOCK_Z;
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+constexpr int SHX = ilog2(BX), SHXY = ilog2(BX * BY);
+static_assert(BX * BY * BZ == CELLS, "a block holds 512 cells");
+static_assert((1 << SHX) == BX && (1 << ilog2(BY)) == BY && (1 << ilog2(BZ)) == BZ,
+              "block extents are powers of two");
+static_assert(BX % 8 == 0 && BY >= 2 && BZ >= 2, "x-rows of whole sectors; a one-cell halo per axis");
+__device__ __forceinline__ int lx_of(int c) { return c & (BX - 1); }
+__device__ __forceinline__ int ly_of(int c) { return (c >> SHX) & (BY - 1); }
+__device__ __forceinline__ int lz_of(int c) { return c >> SHXY; }
+
+// Neighbour-block index (0..26) of a local coordinate in [-1, B].
+template <int B>
+__device__ __forceinline__ int side(int v) { return v < 0 ? 0 : (v > B - 1 ? 2 : 1); }
+__device__ __forceinline__ int nbk(int x, int y, int z) { return side<BX>(x) + 3 * side<BY>(y) + 9 * side<BZ>(z); }
 __device__ __forceinline__ int lcell(int x, int y, int z)
 {
-    return (x & 7) | ((y & 7) << 3) | ((z & 7) << 6);
+    return (x & (BX - 1)) | ((y & (BY - 1)) << SHX) | ((z & (BZ - 1)) << SHXY);
 }
 
 __device__ __forceinline__ int neighbour_block(const KParams &kp, int x, int y, int z)
@@ -307,7 +330,7 @@ __device__ __forceinline__ unsigned reach_bits(int lx, int ly, int lz)
 // solid, cells outside a non-periodic axis are solid; bit HELD_BIT: held).
 __device__ uint32_t cell_bits(const KParams &kp, int gid, int c)
 {
-    const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+    const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
     uint32_t bits = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -353,7 +376,7 @@ __device__ __forceinline__ void dev_issue(const KParams &kp, const WarpNbr &wn, 
                                           int own_slot, int c, uint32_t bits, bool live,
                                           bool own_ambient, DevLoad &L)
 {
-    const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+    const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
     const uint32_t own =
         (own_ambient ? (uint32_t)kp.amb_slot : (uint32_t)own_slot) * (uint32_t)kp.slot_floats + (uint32_t)c;
     const bool held = (bits >> HELD_BIT) & 1u;
@@ -809,7 +832,7 @@ __global__ void __launch_bounds__(THREADS) k_init_dev(KParams kp, int nslots)
     for (int it = blockIdx.x; it < nslots * PARTS; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
         const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
         const bool live = !(bits & 1u);
@@ -908,7 +931,7 @@ __device__ __forceinline__ void criterion_mark(const KParams &kp, Ctrl *ctrl, in
                                                const float u[2][3])
 {
     const int lane = threadIdx.x & 31;
-    const unsigned front = reach_bits(c & 7, (c >> 3) & 7, c >> 6) & wn.amb;
+    const unsigned front = reach_bits(lx_of(c), ly_of(c), lz_of(c)) & wn.amb;
     unsigned tgt = 0;
     if (fluid && front) {
         float d2max = 0.f;
@@ -956,7 +979,7 @@ __device__ __forceinline__ void macro_body(const KParams &kp, int step, int crit
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
@@ -1253,7 +1276,7 @@ __device__ __forceinline__ void activate_body(const KParams &kp, int step)
     for (int it = blockIdx.x; it < ncand * PARTS; it += gridDim.x) {
         const int k = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const int slot = n_old + k;
         const int gid = kp.cand_list[k];
         if (!in_range(kp, gid, (long long)kp.nbx * kp.nby * kp.nbz, 5)) continue;
@@ -1442,7 +1465,7 @@ __device__ __forceinline__ void collide_body(const KParams &kp, int step)
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
@@ -1617,7 +1640,7 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
@@ -1675,7 +1698,7 @@ __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
@@ -1779,7 +1802,7 @@ __device__ __forceinline__ void macro_aa_body(const KParams &kp, int step, int c
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
@@ -1843,7 +1866,7 @@ __device__ __forceinline__ void collide_aa_body(const KParams &kp, int step)
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
@@ -2035,7 +2058,7 @@ template <class Sink>
 __device__ __forceinline__ void pull2_staged(const WarpNbr &wn, const float *rd, const float *st, int c,
                                              uint32_t bits, bool live, Sink &&sink)
 {
-    const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+    const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
     const bool held = (bits >> HELD_BIT) & 1u;
     uint32_t off[Q];
     uint32_t inside = 0;  // bit I: population I comes from the stage
@@ -2116,7 +2139,7 @@ __device__ __forceinline__ void collide2_staged_body(const KParams &kp, int step
         ctrl->fluid_updates += ctrl->fluid_active;
     }
     staged_blocks(kp, rd, n, [&](int slot, int c, const float *st) {
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
         const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
         const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
@@ -2234,7 +2257,7 @@ __device__ __forceinline__ void collide_dev_body(const KParams &kp, int step)
         const bool any_cell = __any_sync(FULL, !(cur.bits & 1u));
         if (cur.ok && any_cell) {  // skip warps of solid cells only
             const int slot = cur.slot, c = cur.c;
-            const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+            const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
             const uint32_t bits = cur.bits;
             const bool nonsolid = !(bits & 1u);
             const bool held = (bits >> HELD_BIT) & 1u;
@@ -2347,7 +2370,7 @@ __global__ void __launch_bounds__(THREADS) k_output(KParams kp, int rdbuf, int c
         const int r = it / PARTS;
         const int slot = slot0 + r;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot), moff);
         const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
         const bool live = !(bits & 1u);
@@ -2411,7 +2434,7 @@ __device__ __forceinline__ void stored_cell(const KParams &kp, int rdbuf, int sl
         const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
         const float4 m = live ? __ldg(mref + (size_t)slot * CELLS + c) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float own[2] = {m.x, m.y};
-        reader_refs<2>(wn, mref, c & 7, (c >> 3) & 7, c >> 6, bits, live, own, rdst);
+        reader_refs<2>(wn, mref, lx_of(c), ly_of(c), lz_of(c), bits, live, own, rdst);
     }
     if constexpr (S::DEV) {
 #pragma unroll
@@ -2425,7 +2448,7 @@ __device__ __forceinline__ void stored_cell(const KParams &kp, int rdbuf, int sl
         // parity of the next step; the initial state is laid out as after a
         // local step)
         const uint32_t own = (uint32_t)slot * (uint32_t)kp.slot_floats + (uint32_t)c;
-        const int lx = c & 7, ly = (c >> 3) & 7, lz = c >> 6;
+        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         if (rdbuf == 0) {
             Unroll<0, Q>::run([&]<int I>() {
                 const uint32_t d = aa_dst<true, I>(WarpNbr{}, own, lx, ly, lz, bits);
@@ -2506,82 +2529,84 @@ template <int NC, int ST>
 __global__ void __launch_bounds__(THREADS) k_features(KParams kp, int par, const int *nsnap,
                                                       const int *list, const int *count, float *feat)
 {
-    using S = Store<ST>;
-    __shared__ float acc[6][4];  // per face: sum rho0, sum rho1, cells, flux
-    const typename S::T *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
-    const float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
-    const int n = *count;
-    const int nmesh = *nsnap;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int b = blockIdx.x; b < n; b += gridDim.x) {
-        const int gid = list[b];
-        float *out = feat + (size_t)b * LBM_MLP_IN;
-        if (warp < 6) {
-            const int axis = warp >> 1, sgn = (warp & 1) ? 1 : -1;  // neighbour at gid + sgn e_axis
-            const int k = 13 + sgn * (axis == 0 ? 1 : (axis == 1 ? 3 : 9));
-            const int nid = neighbour_of(kp, gid, k);
-            const int slot = nid >= 0 ? kp.slot_of[nid] : SOLIDBLK;
-            float r0 = 0.f, r1 = 0.f, cnt = 0.f, flux = 0.f;
-            if (slot >= 0 && slot < nmesh) {
-                const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
-                const int layer = sgn < 0 ? 7 : 0;  // the neighbour's cells touching the block
-#pragma unroll 1
-                for (int pass = 0; pass < 2; ++pass) {
-                    const int idx = pass * 32 + lane, u = idx & 7, v = idx >> 3;
-                    const int lx = axis == 0 ? layer : u, ly = axis == 1 ? layer : (axis == 0 ? u : v),
-                              lz = axis == 2 ? layer : v;
-                    const int c = lx | (ly << 3) | (lz << 6);
-                    const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
-                    const bool use = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
-                    float ref[2] = {0.f, 0.f};
-                    if (S::DEV && use) {
-                        const float4 m = __ldg(mac_prev + (size_t)slot * CELLS + c);
-                        ref[0] = m.x;
-                        ref[1] = m.y;
-                    }
-                    Moments m;
-                    pull_state<NC, ST>(kp, wn, rd, par, slot, c, lx, ly, lz, bits, use, ref,
-                                       [&]<int I>(int a, float f) { m.template add<I>(a, f); });
-                    if (use) {
-                        r0 += m.rho[0];
-                        r1 += NC == 2 ? m.rho[1] : 0.f;
-                        cnt += 1.f;
-                        // into the block: along -sgn e_axis
-                        const float j = m.j[0][axis] + (NC == 2 ? m.j[1][axis] : 0.f);
-                        flux -= (float)sgn * j;
+    if constexpr (BX == 8 && BY == 8 && BZ == 8) {  // the features are defined on 8 x 8 faces
+        using S = Store<ST>;
+        __shared__ float acc[6][4];  // per face: sum rho0, sum rho1, cells, flux
+        const typename S::T *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
+        const float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
+        const int n = *count;
+        const int nmesh = *nsnap;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int b = blockIdx.x; b < n; b += gridDim.x) {
+            const int gid = list[b];
+            float *out = feat + (size_t)b * LBM_MLP_IN;
+            if (warp < 6) {
+                const int axis = warp >> 1, sgn = (warp & 1) ? 1 : -1;  // neighbour at gid + sgn e_axis
+                const int k = 13 + sgn * (axis == 0 ? 1 : (axis == 1 ? 3 : 9));
+                const int nid = neighbour_of(kp, gid, k);
+                const int slot = nid >= 0 ? kp.slot_of[nid] : SOLIDBLK;
+                float r0 = 0.f, r1 = 0.f, cnt = 0.f, flux = 0.f;
+                if (slot >= 0 && slot < nmesh) {
+                    const WarpNbr wn = warp_nbr_of(kp, nbr_row_lane(kp, slot));
+                    const int layer = sgn < 0 ? 7 : 0;  // the neighbour's cells touching the block
+    #pragma unroll 1
+                    for (int pass = 0; pass < 2; ++pass) {
+                        const int idx = pass * 32 + lane, u = idx & 7, v = idx >> 3;
+                        const int lx = axis == 0 ? layer : u, ly = axis == 1 ? layer : (axis == 0 ? u : v),
+                                  lz = axis == 2 ? layer : v;
+                        const int c = lx | (ly << 3) | (lz << 6);
+                        const uint32_t bits = kp.nbits[(size_t)slot * CELLS + c];
+                        const bool use = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+                        float ref[2] = {0.f, 0.f};
+                        if (S::DEV && use) {
+                            const float4 m = __ldg(mac_prev + (size_t)slot * CELLS + c);
+                            ref[0] = m.x;
+                            ref[1] = m.y;
+                        }
+                        Moments m;
+                        pull_state<NC, ST>(kp, wn, rd, par, slot, c, lx, ly, lz, bits, use, ref,
+                                           [&]<int I>(int a, float f) { m.template add<I>(a, f); });
+                        if (use) {
+                            r0 += m.rho[0];
+                            r1 += NC == 2 ? m.rho[1] : 0.f;
+                            cnt += 1.f;
+                            // into the block: along -sgn e_axis
+                            const float j = m.j[0][axis] + (NC == 2 ? m.j[1][axis] : 0.f);
+                            flux -= (float)sgn * j;
+                        }
                     }
                 }
+    #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    r0 += __shfl_xor_sync(FULL, r0, o);
+                    r1 += __shfl_xor_sync(FULL, r1, o);
+                    cnt += __shfl_xor_sync(FULL, cnt, o);
+                    flux += __shfl_xor_sync(FULL, flux, o);
+                }
+                if (lane == 0) {
+                    acc[warp][0] = r0;
+                    acc[warp][1] = r1;
+                    acc[warp][2] = cnt;
+                    acc[warp][3] = flux;
+                }
+            } else if (warp == 6 && lane < 27 && lane != 13) {
+                const int nid = neighbour_of(kp, gid, lane);
+                out[8 + lane - (lane > 13 ? 1 : 0)] = (nid >= 0 && kp.slot_of[nid] >= 0) ? 1.f : 0.f;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                r0 += __shfl_xor_sync(FULL, r0, o);
-                r1 += __shfl_xor_sync(FULL, r1, o);
-                cnt += __shfl_xor_sync(FULL, cnt, o);
-                flux += __shfl_xor_sync(FULL, flux, o);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                float r0 = 0.f, r1 = 0.f, cnt = 0.f;
+                for (int f = 0; f < 6; ++f) {
+                    r0 += acc[f][0];
+                    r1 += acc[f][1];
+                    cnt += acc[f][2];
+                    out[2 + f] = acc[f][3];
+                }
+                out[0] = cnt > 0.f ? r0 / cnt : kp.rho_amb[0];
+                out[1] = cnt > 0.f ? r1 / cnt : kp.rho_amb[1];
             }
-            if (lane == 0) {
-                acc[warp][0] = r0;
-                acc[warp][1] = r1;
-                acc[warp][2] = cnt;
-                acc[warp][3] = flux;
-            }
-        } else if (warp == 6 && lane < 27 && lane != 13) {
-            const int nid = neighbour_of(kp, gid, lane);
-            out[8 + lane - (lane > 13 ? 1 : 0)] = (nid >= 0 && kp.slot_of[nid] >= 0) ? 1.f : 0.f;
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float r0 = 0.f, r1 = 0.f, cnt = 0.f;
-            for (int f = 0; f < 6; ++f) {
-                r0 += acc[f][0];
-                r1 += acc[f][1];
-                cnt += acc[f][2];
-                out[2 + f] = acc[f][3];
-            }
-            out[0] = cnt > 0.f ? r0 / cnt : kp.rho_amb[0];
-            out[1] = cnt > 0.f ? r1 / cnt : kp.rho_amb[1];
-        }
-        __syncthreads();
     }
 }
 

@@ -23,6 +23,7 @@ STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}  # LBM_STORAGE_*
 STREAMING = {"ab": 0, "aa": 1}  # LBM_STREAM_*
 Q = 19
 EDGE = 8
+SHAPES = ((8, 8, 8), (16, 8, 4), (16, 4, 8), (32, 4, 4))  # block shapes of the library
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
@@ -36,6 +37,7 @@ class Params(C.Structure):
         ("progressive", C.c_int),
         ("storage", C.c_int),
         ("streaming", C.c_int),
+        ("block", C.c_int * 3),
         ("tau", C.c_double), ("beta", C.c_double),
         ("pr_a", C.c_double), ("pr_b", C.c_double), ("pr_R", C.c_double), ("pr_omega", C.c_double),
         ("T_over_Tc", C.c_double),
@@ -184,7 +186,8 @@ class LBM:
 
     Keyword parameters mirror lbm_params: nx, ny, nz, ncomp, periodic,
     progressive, storage ("fp32", "fp16", "bf16" or the LBM_STORAGE_* code),
-    streaming ("ab" or "aa", the LBM_STREAM_* pattern),
+    streaming ("ab" or "aa", the LBM_STREAM_* pattern), block (cells per
+    block along x, y, z: one of SHAPES),
     tau, beta, pr_a, pr_b, pr_R, pr_omega, T_over_Tc, g_self, g_cross, g_ads,
     grav, rho_ref, S, max_blocks.  ``stream``: a
     torch.cuda.Stream (default: the current stream).  ``torch_alloc``:
@@ -202,7 +205,11 @@ class LBM:
         p = Params()
         p.nx, p.ny, p.nz = int(kw["nx"]), int(kw["ny"]), int(kw["nz"])
         self.shape = (p.nz, p.ny, p.nx)
-        self.nblocks = (p.nx // EDGE) * (p.ny // EDGE) * (p.nz // EDGE)
+        blk = tuple(int(v) for v in kw.get("block", (8, 8, 8)))
+        for a in range(3):
+            p.block[a] = blk[a]
+        self.block = blk
+        self.nblocks = (p.nx // blk[0]) * (p.ny // blk[1]) * (p.nz // blk[2])
         p.ncomp = int(kw.get("ncomp", 2))
         self.ncomp = p.ncomp
         per = kw.get("periodic", (1, 1, 0))
@@ -435,9 +442,12 @@ class MLP:
 
 
 def from_case(case, **over):
-    """Context + geometry from a workloads case dict."""
+    """Context + geometry from a workloads case dict.  The case's block
+    shape is used when the library has it (SHAPES), else 8^3."""
     p = dict(case["params"])
-    p.pop("block", None)
+    blk = p.pop("block", None)
+    if blk is not None and tuple(blk) in SHAPES:
+        p["block"] = tuple(blk)
     p.update(over)
     sim = LBM(**p)
     sim.set_geometry(case["cell_type"], case["rho_init"], case["u_init"], case["rho_amb"])

@@ -70,12 +70,20 @@ def _params(**over):
     p.pr_a, p.pr_b, p.pr_R, p.pr_omega, p.T_over_Tc = 2 / 49, 2 / 21, 1.0, 0.344, 0.85
     p.g_self = -1.0
     for k, v in over.items():
-        setattr(p, k, v)
+        if k == "block":
+            for a in range(3):
+                p.block[a] = v[a]
+        else:
+            setattr(p, k, v)
     return p
 
 
 @pytest.mark.parametrize("over,frag", [
-    (dict(nx=12), "multiple of 8"),
+    (dict(nx=12), "multiple of the 8x8x8 block"),
+    (dict(block=(4, 4, 4)), "unsupported block shape"),
+    (dict(block=(8, 8, 4)), "unsupported block shape"),
+    (dict(block=(32, 4, 4)), "multiple of the 32x4x4 block"),
+    (dict(block=(16, 8, 4), storage=1), "need the FP32 storage form"),
     (dict(ncomp=3), "ncomp"),
     (dict(tau=0.5), "tau"),
     (dict(S=-1.0), "S must be"),
