@@ -134,3 +134,31 @@ def test_aa_halves_population_memory_and_refuses_other_modes(L):
         assert e.value.code == L.EINVAL
     ab.close()
     aa.close()
+
+
+def test_aa_pool_exhaustion_keeps_last_complete_step(L):
+    """A pool too small for the blocks a step creates: LBM_ENOMEM, and the
+    in-place array still holds the last completed step (the failing step's
+    collision never ran), equal to the A-B run stopped there."""
+    case = W.drop_in_box()
+    small = L.from_case(case, streaming="aa", max_blocks=12)
+    ref = L.from_case(case)
+    failed_at = None
+    for t in range(40):
+        try:
+            small.step(1)
+        except L.LBMError as e:
+            assert e.code == L.ENOMEM
+            failed_at = t
+            break
+        ref.step(1)
+    assert failed_at is not None
+    assert small.stats()["steps"] == failed_at
+    for a in range(2):
+        for x, y in zip(small.macro(a), ref.macro(a)):
+            np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(small.mass(), ref.mass())
+    with pytest.raises(L.LBMError):
+        small.step(1)
+    small.close()
+    ref.close()
