@@ -47,6 +47,7 @@ struct lbm_ctx {
     int ctas_per_sm = 1;
     int nbx = 0, nby = 0, nbz = 0;
     int bx = EDGE, by = EDGE, bz = EDGE;  // cells per block along x, y, z
+    std::vector<long long> cell_off;     // [CELLS]: grid offset of a block's cell from its origin
     long long nblocks = 0;
     int capacity = 0;
     bool geometry = false;
@@ -183,10 +184,13 @@ void release(lbm_ctx *c, void *ptr)
         }
 }
 
-// Cell index inside its block: x + bx (y + by z) in block-local coordinates.
-int local_cell(const lbm_ctx *c, int x, int y, int z)
+// Grid index of the first cell of block b (its origin); cell lc of the
+// block (lc = x + bx (y + by z) in block-local coordinates) is at
+// block_origin + cell_off[lc].
+long long block_origin(const lbm_ctx *c, long long b)
 {
-    return (x % c->bx) + c->bx * ((y % c->by) + c->by * (z % c->bz));
+    const long long ix = b % c->nbx, iy = (b / c->nbx) % c->nby, iz = b / ((long long)c->nbx * c->nby);
+    return ix * c->bx + (long long)c->p.nx * (iy * c->by + (long long)c->p.ny * (iz * c->bz));
 }
 
 // Index of the block shape p asks for in BLOCK_SHAPES ({0, 0, 0}: the
@@ -500,6 +504,9 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
     c->nbx = p->nx / sh.x;
     c->nby = p->ny / sh.y;
     c->nbz = p->nz / sh.z;
+    c->cell_off.resize(CELLS);
+    for (int lc = 0; lc < CELLS; ++lc)
+        c->cell_off[lc] = lc % sh.x + (long long)p->nx * ((lc / sh.x) % sh.y + (long long)p->ny * (lc / (sh.x * sh.y)));
     c->nblocks = (long long)c->nbx * c->nby * c->nbz;
     long long cap = p->max_blocks > 0 ? std::min<long long>(p->max_blocks, c->nblocks) : c->nblocks;
     c->capacity = (int)cap;
@@ -628,12 +635,17 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     c->held_h.assign(nb * MASK_WORDS, 0u);
     c->nonsolid_h.assign(nb, 0);
     std::vector<char> differs(nb, 0);
+    // block index and block-local part of each coordinate, per axis
+    std::vector<int> qx(p.nx), rx(p.nx), qy(p.ny), ry(p.ny), qz(p.nz), rz(p.nz);
+    for (int x = 0; x < p.nx; ++x) qx[x] = x / c->bx, rx[x] = x % c->bx;
+    for (int y = 0; y < p.ny; ++y) qy[y] = y / c->by, ry[y] = (y % c->by) * c->bx;
+    for (int z = 0; z < p.nz; ++z) qz[z] = z / c->bz, rz[z] = (z % c->bz) * c->bx * c->by;
     for (int z = 0; z < p.nz; ++z)
         for (int y = 0; y < p.ny; ++y)
             for (int x = 0; x < p.nx; ++x) {
                 const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
-                const long long b = (x / c->bx) + c->nbx * ((long long)(y / c->by) + (long long)c->nby * (z / c->bz));
-                const int lc = local_cell(c, x, y, z);
+                const long long b = qx[x] + c->nbx * ((long long)qy[y] + (long long)c->nby * qz[z]);
+                const int lc = rx[x] + ry[y] + rz[z];
                 if (cell_type[i] == LBM_CELL_SOLID) {
                     c->solid_h[b * MASK_WORDS + (lc >> 5)] |= 1u << (lc & 31);
                     continue;
@@ -751,14 +763,11 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     for (int s0 = 0; s0 < n0; s0 += per_chunk) {
         const int m = std::min(per_chunk, n0 - s0);
         for (int r = 0; r < m; ++r) {
-            const int b = block_of[s0 + r];
-            const int bx = b % c->nbx, by = (b / c->nbx) % c->nby, bz = b / (c->nbx * c->nby);
+            const long long o = block_origin(c, block_of[s0 + r]);
             for (int a = 0; a < nc; ++a) {
                 float *dst = host.data() + ((size_t)r * nc + a) * 4 * CELLS;
                 for (int lc = 0; lc < CELLS; ++lc) {
-                    const int x = bx * c->bx + lc % c->bx, y = by * c->by + (lc / c->bx) % c->by,
-                              z = bz * c->bz + lc / (c->bx * c->by);
-                    const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
+                    const long long i = o + c->cell_off[lc];
                     dst[lc] = rho_init[a * ncell + i];
                     for (int d = 0; d < 3; ++d)
                         dst[(d + 1) * CELLS + lc] = u_init ? u_init[(a * 3 + d) * ncell + i] : 0.f;
@@ -817,12 +826,9 @@ int lbm_get_macro(lbm_ctx *c, int comp, float *rho, float *ux, float *uy, float 
     float *outs[4] = {rho, ux, uy, uz};
     // unmeshed and solid cells first
     for (long long b = 0; b < c->nblocks; ++b) {
-        const int bx = (int)(b % c->nbx), by = (int)((b / c->nbx) % c->nby),
-                  bz = (int)(b / ((long long)c->nbx * c->nby));
+        const long long o = block_origin(c, b);
         for (int lc = 0; lc < CELLS; ++lc) {
-            const int x = bx * c->bx + lc % c->bx, y = by * c->by + (lc / c->bx) % c->by,
-                      z = bz * c->bz + lc / (c->bx * c->by);
-            const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
+            const long long i = o + c->cell_off[lc];
             const bool sol = (c->solid_h[b * MASK_WORDS + (lc >> 5)] >> (lc & 31)) & 1u;
             if (rho) rho[i] = sol ? 0.f : c->rho_amb[comp];
             for (int m = 1; m < 4; ++m)
@@ -850,12 +856,9 @@ int lbm_get_macro(lbm_ctx *c, int comp, float *rho, float *ux, float *uy, float 
                                         cudaMemcpyDeviceToHost, c->stream));
         CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
         for (int r = 0; r < m; ++r) {
-            const int b = block_of[s0 + r];
-            const int bx = b % c->nbx, by = (b / c->nbx) % c->nby, bz = b / (c->nbx * c->nby);
+            const long long o = block_origin(c, block_of[s0 + r]);
             for (int lc = 0; lc < CELLS; ++lc) {
-                const int x = bx * c->bx + lc % c->bx, y = by * c->by + (lc / c->bx) % c->by,
-                      z = bz * c->bz + lc / (c->bx * c->by);
-                const long long i = x + (long long)p.nx * (y + (long long)p.ny * z);
+                const long long i = o + c->cell_off[lc];
                 for (int q = 0; q < 4; ++q)
                     if (outs[q]) outs[q][i] = host[((size_t)r * 4 + q) * CELLS + lc];
             }
