@@ -156,12 +156,13 @@ def make_case(S=None, size=256, workload="injection", block="8x8x8"):
 
 
 def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32", proposer=None,
-              exec_mode="stream", streaming="ab"):
+              exec_mode="stream", streaming="ab", slot_order=64):
     """Warm up, then time `steps` steps one by one (L2 flushed before each).
     proposer: an lbm MLP to run the activation proposer with (period 16,
     threshold 0.5).  streaming: "ab" or "aa" (one population array)."""
     sim = L.from_case(case, progressive=progressive, storage=storage, streaming=streaming)
     sim.set_exec(exec_mode)
+    sim.set_slot_order(slot_order)
     if proposer is not None:
         sim.set_proposer(proposer, period=16, threshold=0.5)
     sim.step(warmup)
@@ -196,6 +197,7 @@ def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="
         nonsolid_blocks=st1["nonsolid_blocks"],
         total_blocks=st1["total_blocks"],
         device_bytes=st1["device_bytes"],
+        slot_sorts=st1["slot_sorts"],
         clocks=clk.summary(),
     )
     sim.close()
@@ -385,6 +387,8 @@ def main():
                     help="how the library enqueues the steps")
     ap.add_argument("--block", default="8x8x8", choices=["8x8x8", "16x8x4", "16x4x8", "32x4x4"],
                     help="cells per block along x, y, z")
+    ap.add_argument("--slot-order", type=int, default=64,
+                    help="steps between checks for renumbering the meshed slots in block order (0: never)")
     ap.add_argument("--streaming", default="ab", choices=["ab", "aa"],
                     help="population streaming pattern: two arrays (A-B) or one updated in place (A-A)")
     ap.add_argument("--no-forms", action="store_true",
@@ -423,7 +427,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, args.storage,
-                     exec_mode=args.exec, streaming=args.streaming)
+                     exec_mode=args.exec, streaming=args.streaming, slot_order=args.slot_order)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -503,6 +507,7 @@ def main():
         "mode": "progressive", "grid": [case["params"][k] for k in ("nx", "ny", "nz")],
         "block": list(case["params"]["block"]),
         "storage": args.storage, "exec": args.exec, "streaming": args.streaming,
+        "slot_order_period": args.slot_order, "slot_sorts": prog["slot_sorts"],
         "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
         "mean_active_fraction": round(prog["cells"] / 512 / args.steps / prog["total_blocks"], 4),

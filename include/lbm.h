@@ -147,6 +147,7 @@ typedef struct lbm_stats {
     long long created_blocks;   /* blocks created by the criterion since lbm_set_geometry */
     long long prepared_blocks;  /* blocks the activation proposer prepared */
     long long prepared_hits;    /* created blocks that had been prepared */
+    long long slot_sorts;       /* renumberings of the meshed slots in block order */
 } lbm_stats;
 
 /* Validate `p`, allocate the block pool (capacity x 2 buffers x ncomp x 19 x
@@ -275,6 +276,16 @@ int lbm_mass_noalloc(const float *f, const uint32_t *solid, long long nblocks, i
  * Errors: LBM_EINVAL (unknown mode, or no cooperative launch on the
  * device). */
 int lbm_set_exec(lbm_ctx *ctx, int mode);
+
+/* Slot order (progressive mesh).  A created block takes the next free slot
+ * of the pool, so the slot order drifts from the spatial order and the
+ * step's memory accesses lose locality.  Every `period` steps (default 64;
+ * 0 = never) the device checks whether the blocks created since the last
+ * renumbering reach 1/16 of the meshed ones and, if so, renumbers the meshed
+ * slots in block order between two steps (moving the populations through
+ * the idle population buffer; not with A-A streaming).  Results are the same
+ * bit for bit with any period.  Errors: LBM_EINVAL (period < 0). */
+int lbm_set_slot_order(lbm_ctx *ctx, int period);
 
 /* Test hook of the bounded device wait: one cooperative launch whose grid
  * barrier expects `missing` more CTAs than it has, polling at most `spins`

@@ -91,6 +91,8 @@ struct lbm_ctx {
     float threshold = 0.5f;
     cudaStream_t side = nullptr;
     cudaEvent_t side_ev = nullptr;
+    cudaEvent_t side_done = nullptr;  // end of the side stream's last proposer round
+    int sort_period = 64;             // steps between checks for renumbering the slots (0: never)
     // execution mode
     int exec = LBM_EXEC_STREAM;
     cudaStream_t cap = nullptr;        // capture stream of the step graph
@@ -360,6 +362,7 @@ int enqueue_proposer(lbm_ctx *c, int t)
     CUDA_OR_FAIL(c, mlp_forward_on(c->mlp, c->pfeat, (int)c->nblocks, c->pcount, 1, c->pprob, c->side));
     CUDA_OR_FAIL(c, launch_prepare(k, c->plist, c->pcount, c->pprob, c->threshold, c->prep, c->nbits_pre,
                                    c->sms, c->side));
+    CUDA_OR_FAIL(c, cudaEventRecord(c->side_done, c->side));
     c->launches += 4;
     return LBM_OK;
 }
@@ -401,18 +404,33 @@ int ensure_graph(lbm_ctx *c)
     return LBM_OK;
 }
 
+// Whether the slots may need renumbering in block order before step t (the
+// device decides whether they do; A-A streaming has no idle buffer to move
+// them through).
+bool sort_point(const lbm_ctx *c, int t)
+{
+    return c->sort_period > 0 && c->p.progressive && !c->kp.aa && t > 0 && t % c->sort_period == 0;
+}
+
 int enqueue_steps(lbm_ctx *c, int nsteps)
 {
     int k = 0;
     while (k < nsteps) {
         const int t = (int)(c->step + k);
+        if (sort_point(c, t)) {
+            // the side stream reads the tables: let its last round finish
+            if (c->mlp) CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->stream, c->side_done, 0));
+            CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return launch_sort(c->kp, c->sms, c->stream); }, 6));
+        }
         if (c->mlp && t % c->period == 0) {
             int rc = enqueue_proposer(c, t);
             if (rc) return rc;
         }
-        // steps up to the next proposer round
+        // steps up to the next proposer round or renumbering check
         int chunk = nsteps - k;
         if (c->mlp) chunk = std::min(chunk, c->period - t % c->period);
+        if (c->sort_period > 0 && c->p.progressive && !c->kp.aa)
+            chunk = std::min(chunk, c->sort_period - t % c->sort_period);
         if (c->exec == LBM_EXEC_PERSISTENT) {
             CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] {
                              return launch_run(c->kp, chunk, c->p.progressive ? 1 : 0, c->sms, c->stream);
@@ -599,6 +617,7 @@ int lbm_destroy(lbm_ctx *c)
     flush_profile(c);
     free_all(c);
     if (c->side_ev) cudaEventDestroy(c->side_ev);
+    if (c->side_done) cudaEventDestroy(c->side_done);
     if (c->side) cudaStreamDestroy(c->side);
     drop_graph(c);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -978,6 +997,7 @@ int lbm_get_stats(lbm_ctx *c, lbm_stats *out)
         out->created_blocks = (long long)ctrl.created;
         out->prepared_blocks = (long long)ctrl.prepared;
         out->prepared_hits = (long long)ctrl.prepared_hits;
+        out->slot_sorts = (long long)ctrl.sorts;
         long long ns = 0;
         for (int v : c->nonsolid_h) ns += v > 0;
         out->nonsolid_blocks = ns;
@@ -1085,6 +1105,7 @@ int lbm_set_proposer(lbm_ctx *c, lbm_mlp *mlp, int period, float threshold)
     if (!c->side) {
         CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->side_ev, cudaEventDisableTiming));
+        CUDA_OR_FAIL(c, cudaEventCreateWithFlags(&c->side_done, cudaEventDisableTiming));
     }
     c->mlp = mlp;
     c->period = period;
@@ -1111,6 +1132,14 @@ int lbm_set_exec(lbm_ctx *c, int mode)
     c->exec = mode;
     c->kp.staged = mode == LBM_EXEC_STAGED ? 1 : 0;
     drop_graph(c);
+    return LBM_OK;
+}
+
+int lbm_set_slot_order(lbm_ctx *c, int period)
+{
+    if (!c) return LBM_EINVAL;
+    if (period < 0) return fail(c, LBM_EINVAL, "period must be >= 0");
+    c->sort_period = period;
     return LBM_OK;
 }
 

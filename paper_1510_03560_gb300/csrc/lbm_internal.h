@@ -48,6 +48,9 @@ struct Ctrl {
     float psi_amb;     // psi of the ambient density, evaluated on the device
     int check_site;    // checked builds: first failed index check (site id)
     long long check_value;  // and the offending value
+    unsigned long long sorted_created;  // `created` at the last renumbering of the slots
+    unsigned long long sorts;           // renumberings of the slots in block order
+    int sort_go;       // the renumbering under way moves the slots
 };
 
 // Everything a kernel needs, passed by value.
@@ -133,6 +136,8 @@ struct StorageOps {
     int (*ctas_per_sm)();
     // nsteps whole steps in one cooperative launch
     cudaError_t (*run)(const KParams &, int, int, int, cudaStream_t);
+    // between steps: renumber the meshed slots in block order when due
+    cudaError_t (*sort)(const KParams &, int, cudaStream_t);
 };
 const StorageOps *storage_ops_fp32();
 const StorageOps *storage_ops_fp32_16x8x4();
@@ -160,6 +165,7 @@ cudaError_t launch_output(const KParams &kp, int rd, int comp, int slot0, int ns
 cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, double *out, int grid,
                         cudaStream_t s);
 // FP32 populations of one slot of buffer rd into out[ncomp][Q][CELLS] (16-bit forms).
+cudaError_t launch_sort(const KParams &kp, int sms, cudaStream_t s);
 cudaError_t launch_block_pops(const KParams &kp, int rd, int slot, float *out, cudaStream_t s);
 // nsteps steps in one cooperative launch with grid barriers between the
 // phases (bounded waits: a barrier that does not complete sets

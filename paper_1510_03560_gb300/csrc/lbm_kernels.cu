@@ -6,13 +6,17 @@
 namespace lbm {
 namespace {
 
-// Fixed-order sum of the per-slot partial masses into out[0..1].
-__global__ void __launch_bounds__(1024) k_mass_final(const double *partial, int n, double *out)
+// Fixed-order sum of the per-slot partial masses into out[0..1], taken in
+// block order, so that the result does not depend on the slot numbering.
+__global__ void __launch_bounds__(1024) k_mass_final(KParams kp, const double *partial, int n, double *out)
 {
     __shared__ double red[1024][2];
     const int t = threadIdx.x;
+    const int nb = kp.nbx * kp.nby * kp.nbz;
     double s0 = 0.0, s1 = 0.0;
-    for (int i = t; i < n; i += 1024) {
+    for (int b = t; b < nb; b += 1024) {
+        const int i = kp.slot_of[b];
+        if (i < 0 || i >= n) continue;
         s0 += partial[(size_t)i * 2];
         s1 += partial[(size_t)i * 2 + 1];
     }
@@ -141,9 +145,11 @@ cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, doubl
 {
     cudaError_t e = ops_of(kp).mass_partial(kp, rd, n, partial, grid, s);
     if (e != cudaSuccess) return e;
-    k_mass_final<<<1, 1024, 0, s>>>(partial, n, out);
+    k_mass_final<<<1, 1024, 0, s>>>(kp, partial, n, out);
     return cudaGetLastError();
 }
+
+cudaError_t launch_sort(const KParams &kp, int sms, cudaStream_t s) { return ops_of(kp).sort(kp, sms, s); }
 
 cudaError_t launch_block_pops(const KParams &kp, int rd, int slot, float *out, cudaStream_t s)
 {

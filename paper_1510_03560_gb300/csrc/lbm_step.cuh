@@ -1113,40 +1113,30 @@ __global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KPara
     macro_dev_body<NC, ST>(kp, kp.ctrl->step, criterion);
 }
 
-// Deterministic compaction of the candidates of a step (one CTA): the
-// criterion marks candidates in any order (cand_mark 1, a provisional slot);
-// here they are renumbered in ascending block order, slot n_old + rank, by
-// a prefix scan over the marks.  The marks go in tiles of 32 per thread: a
-// thread gets its 32 consecutive marks as a bit mask (warp ballots over
-// coalesced rows), a
+// Ranks in ascending block order of the blocks b < nb with pick(b), by a
+// prefix scan in tiles of 32 blocks per thread: a thread gets its 32
+// consecutive flags as a bit mask (warp ballots over coalesced rows), a
 // warp-shuffle scan and a scan of the warp totals give its first rank, and
-// the candidates are written from the mask; a running total carries the
-// ranks from tile to tile.  Block creation then sets the mark to 2 (meshed).
-// Nothing is done when the pool cannot hold the candidates (block creation
-// undoes them).  Every thread of the CTA must call.
-__device__ __forceinline__ void order_body(const KParams &kp, int step)
+// emit(b, rank) runs for its picked blocks; a running total carries the ranks
+// from tile to tile.  Every thread of the CTA must call.
+template <class Pick, class Emit>
+__device__ __forceinline__ void scan_blocks(int nb, Pick &&pick, Emit &&emit)
 {
-    constexpr int W = 32;  // marks per thread and tile
+    constexpr int W = 32;  // flags per thread and tile
     __shared__ int warp_sum[32];
-    Ctrl *ctrl = kp.ctrl;
-    const int par = step & 1;
-    const int n_old = ctrl->n_active[par];
-    const int ncand = ctrl->ncand[par];
-    if (ctrl->status || ncand <= 0 || n_old + ncand > kp.capacity) return;
-    const int nb = kp.nbx * kp.nby * kp.nbz;
     const int T = blockDim.x, t = threadIdx.x;
     const int lane = t & 31, warp = t >> 5, nwarps = T >> 5;
-    int carry = 0;  // candidates in the tiles before this one
+    int carry = 0;  // picked blocks in the tiles before this one
     for (int base = 0; base < nb; base += T * W) {
         const int lo = base + t * W;
-        // a warp reads its 32 x 32 marks one coalesced row at a time; lane k
-        // keeps the ballot of row k, i.e. the marks lo .. lo + 31 of its own
+        // a warp reads its 32 x 32 flags one coalesced row at a time; lane k
+        // keeps the ballot of row k, i.e. the flags lo .. lo + 31 of its own
         const int wbase = base + warp * 32 * W;
         uint32_t m = 0;
 #pragma unroll
         for (int k = 0; k < W; ++k) {
             const int b = wbase + k * 32 + lane;
-            const unsigned row = __ballot_sync(FULL, b < nb && kp.cand_mark[b] == 1u);
+            const unsigned row = __ballot_sync(FULL, b < nb && pick(b));
             if (lane == k) m = row;
         }
         const int cnt = __popc(m);
@@ -1174,15 +1164,168 @@ __device__ __forceinline__ void order_body(const KParams &kp, int step)
         while (m) {
             const int b = lo + __ffs(m) - 1;
             m &= m - 1u;
-            kp.cand_list[r] = b;
-            kp.slot_of[b] = n_old + r;
+            emit(b, r);
             ++r;
         }
         __syncthreads();  // warp_sum is rewritten by the next tile
     }
 }
 
+// Deterministic compaction of the candidates of a step (one CTA): the
+// criterion marks candidates in any order (cand_mark 1, a provisional slot);
+// here they are renumbered in ascending block order, slot n_old + rank
+// (scan_blocks over the marks).  Block creation then sets the mark to 2
+// (meshed).
+// Nothing is done when the pool cannot hold the candidates (block creation
+// undoes them).  Every thread of the CTA must call.
+__device__ __forceinline__ void order_body(const KParams &kp, int step)
+{
+    Ctrl *ctrl = kp.ctrl;
+    const int par = step & 1;
+    const int n_old = ctrl->n_active[par];
+    const int ncand = ctrl->ncand[par];
+    if (ctrl->status || ncand <= 0 || n_old + ncand > kp.capacity) return;
+    scan_blocks(
+        kp.nbx * kp.nby * kp.nbz, [&](int b) { return kp.cand_mark[b] == 1u; },
+        [&](int b, int r) {
+            kp.cand_list[r] = b;
+            kp.slot_of[b] = n_old + r;
+        });
+}
+
 __global__ void __launch_bounds__(1024) k_order(KParams kp) { order_body(kp, kp.ctrl->step); }
+
+// ---- slot order ---------------------------------------------------------------
+// Blocks created by the criterion take the next free slots, so the slot
+// order drifts from the spatial order: a block's neighbours are no longer
+// processed near it in time and the sectors they share miss L2 (the same
+// meshed set runs its passes about 10 % faster per cell in block order than
+// in creation order).  Between steps the meshed slots are renumbered in
+// block order once the blocks created since the last renumbering reach
+// 1/16 of the meshed ones: k_sort_rank decides and ranks the blocks
+// (perm[new slot] = old slot, in cand_list, free between steps),
+// k_sort_move / k_sort_back move the populations of the next step's read
+// buffer through the other buffer (idle between steps), k_sort_aux does the
+// same for the solid words, the previous velocities, the 16-bit forms'
+// previous densities and block_of, and k_sort_tables
+// rebuilds the neighbour-slot table.  The launches after k_sort_rank return
+// at once when it decided not to move.  No cell's arithmetic changes: the
+// results are the same bit for bit.
+
+__global__ void __launch_bounds__(1024) k_sort_rank(KParams kp)
+{
+    __shared__ int go;
+    Ctrl *ctrl = kp.ctrl;
+    const int n = ctrl->n_active[ctrl->step & 1];
+    if (threadIdx.x == 0) {
+        go = ctrl->status == 0 && n > 0 &&
+             (ctrl->created - ctrl->sorted_created) * 16ull >= (unsigned long long)n;
+        ctrl->sort_go = go;
+    }
+    __syncthreads();
+    if (!go) return;
+    scan_blocks(
+        kp.nbx * kp.nby * kp.nbz, [&](int b) { return kp.slot_of[b] >= 0; },
+        [&](int b, int r) { kp.cand_list[r] = kp.slot_of[b]; });
+}
+
+// dst[new][k] = src[perm[new]][k] over `words` words per slot, or a plain
+// copy when perm is NULL.
+template <class T>
+__device__ __forceinline__ void sort_copy(const T *src, T *dst, const int *perm, int n, int words)
+{
+    const size_t total = (size_t)n * words;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int s2 = (int)(e / words), k = (int)(e % words);
+        const int s = perm ? perm[s2] : s2;
+        dst[(size_t)s2 * words + k] = src[(size_t)s * words + k];
+    }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(THREADS) k_sort_move(KParams kp)
+{
+    const Ctrl *ctrl = kp.ctrl;
+    if (!ctrl->sort_go) return;
+    const int par = ctrl->step & 1;
+    const typename Store<ST>::T *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
+    typename Store<ST>::T *tmp = pops<ST>(kp) + (size_t)(par ^ 1) * kp.buf_stride;
+    sort_copy(rd, tmp, kp.cand_list, ctrl->n_active[par], kp.slot_floats);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(THREADS) k_sort_back(KParams kp)
+{
+    const Ctrl *ctrl = kp.ctrl;
+    if (!ctrl->sort_go) return;
+    const int par = ctrl->step & 1;
+    typename Store<ST>::T *rd = pops<ST>(kp) + (size_t)par * kp.buf_stride;
+    const typename Store<ST>::T *tmp = pops<ST>(kp) + (size_t)(par ^ 1) * kp.buf_stride;
+    sort_copy(tmp, rd, (const int *)nullptr, ctrl->n_active[par], kp.slot_floats);
+}
+
+// The per-slot words of the other arrays (solid words, previous velocities,
+// 16-bit forms' previous densities as a float4 per cell, block_of) into slot
+// `new` of the other population buffer, packed, or back (BACK).
+template <int ST, bool BACK>
+__global__ void __launch_bounds__(THREADS) k_sort_aux(KParams kp)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (!ctrl->sort_go) return;
+    const int par = ctrl->step & 1;
+    const int n = ctrl->n_active[par];
+    uint32_t *tmp = reinterpret_cast<uint32_t *>(pops<ST>(kp) + (size_t)(par ^ 1) * kp.buf_stride);
+    uint32_t *uprev = reinterpret_cast<uint32_t *>(kp.uprev);
+    uint32_t *macp = reinterpret_cast<uint32_t *>(kp.mac + (size_t)(par ^ 1) * kp.mac_stride);
+    const int nup = kp.uprev ? kp.ncomp * 3 * CELLS : 0;
+    const int nmac = Store<ST>::DEV ? 4 * CELLS : 0;
+    const int words = CELLS + nup + nmac + 1;
+    const size_t total = (size_t)n * words;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const int s2 = (int)(e / words), k = (int)(e % words);
+        uint32_t *t = tmp + (size_t)s2 * kp.slot_floats + k;
+        uint32_t *a;  // the word in its own array, at the old slot (move) or the new one (back)
+        const int s = BACK ? s2 : kp.cand_list[s2];
+        if (k < CELLS)
+            a = kp.nbits + (size_t)s * CELLS + k;
+        else if (k < CELLS + nup)
+            a = uprev + (size_t)s * nup + (k - CELLS);
+        else if (k < CELLS + nup + nmac)
+            a = macp + (size_t)s * nmac + (k - CELLS - nup);
+        else
+            a = reinterpret_cast<uint32_t *>(kp.block_of + s);
+        if (BACK) {
+            *a = *t;
+            if (k == words - 1) kp.slot_of[(int)*t] = s2;
+        } else {
+            *t = *a;
+        }
+    }
+}
+
+// The neighbour-slot table of the renumbered slots (as warp_nbr), and the
+// bookkeeping of the renumbering.
+__global__ void __launch_bounds__(THREADS) k_sort_tables(KParams kp)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (!ctrl->sort_go) return;
+    const int n = ctrl->n_active[ctrl->step & 1];
+    const int lane = threadIdx.x & 31;
+    for (int s = blockIdx.x * (THREADS / 32) + (threadIdx.x >> 5); s < n; s += gridDim.x * (THREADS / 32)) {
+        int v = SOLIDBLK;
+        if (lane == 13) {
+            v = s;
+        } else if (lane < 27) {
+            const int nid = neighbour_of(kp, kp.block_of[s], lane);
+            if (nid >= 0) v = kp.slot_of[nid];
+        }
+        kp.nbr[(size_t)s * NBR_STRIDE + lane] = v;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->sorted_created = ctrl->created;
+        ctrl->sorts += 1ull;
+    }
+}
 
 // A-A: one cell of a block created in this step.  Its incoming
 // populations, as the A-B pull reads them (a meshed neighbour's value
@@ -2870,10 +3013,21 @@ struct Launch {
         }
         return a < b ? a : b;
     }
+    static cudaError_t sort(const KParams &kp, int sms, cudaStream_t s)
+    {
+        k_sort_rank<<<1, 1024, 0, s>>>(kp);
+        k_sort_move<ST><<<sms * 4, THREADS, 0, s>>>(kp);
+        k_sort_back<ST><<<sms * 4, THREADS, 0, s>>>(kp);
+        k_sort_aux<ST, false><<<sms * 4, THREADS, 0, s>>>(kp);
+        k_sort_aux<ST, true><<<sms * 4, THREADS, 0, s>>>(kp);
+        k_sort_tables<<<sms * 2, THREADS, 0, s>>>(kp);
+        return cudaGetLastError();
+    }
     static const StorageOps *ops()
     {
         static const StorageOps table = {init,    init_finish,  ambient_slot, macro,    activate,    collide,
-                                         output,  mass_partial, block_pops,   features, ctas_per_sm, run};
+                                         output,  mass_partial, block_pops,   features, ctas_per_sm, run,
+                                         sort};
         return &table;
     }
 };

@@ -60,7 +60,7 @@ class Stats(C.Structure):
         ("launches", C.c_longlong), ("device_bytes", C.c_longlong),
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_longlong * 4),
         ("created_blocks", C.c_longlong), ("prepared_blocks", C.c_longlong),
-        ("prepared_hits", C.c_longlong),
+        ("prepared_hits", C.c_longlong), ("slot_sorts", C.c_longlong),
     ]
 
 
@@ -70,7 +70,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_step", "lbm_ste
            "lbm_last_error", "lbm_mass_noalloc", "lbm_frontier_features", "lbm_activation_steps",
            "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_set_params", "lbm_mlp_get_params",
            "lbm_mlp_set_scaling", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
-           "lbm_set_proposer", "lbm_set_exec", "lbm_barrier_selftest"]
+           "lbm_set_proposer", "lbm_set_exec", "lbm_barrier_selftest", "lbm_set_slot_order"]
 NOALLOC_MAX_BLOCKS = 65536
 MLP_IN, MLP_HIDDEN = 34, 64
 MLP_NPARAM = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
@@ -123,6 +123,7 @@ def load():
     lib.lbm_set_proposer.argtypes = [vp, vp, C.c_int, C.c_float]
     lib.lbm_set_exec.argtypes = [vp, C.c_int]
     lib.lbm_barrier_selftest.argtypes = [C.c_int, C.c_longlong]
+    lib.lbm_set_slot_order.argtypes = [vp, C.c_int]
     for name in EXPORTS:
         if name != "lbm_last_error":
             getattr(lib, name).restype = C.c_int
@@ -367,6 +368,15 @@ def barrier_selftest(missing: int, spins: int) -> int:
 
 
 LBM.set_exec = _lbm_set_exec
+
+
+def _lbm_set_slot_order(self, period: int):
+    """Check for renumbering the meshed slots in block order every `period`
+    steps (0 = never; lbm_set_slot_order)."""
+    self._check(self.lib.lbm_set_slot_order(self.h, int(period)))
+
+
+LBM.set_slot_order = _lbm_set_slot_order
 LBM.frontier_features = _lbm_frontier_features
 LBM.activation_steps = _lbm_activation_steps
 LBM.set_proposer = _lbm_set_proposer
