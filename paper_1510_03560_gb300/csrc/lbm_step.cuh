@@ -1203,11 +1203,12 @@ __global__ void __launch_bounds__(1024) k_order(KParams kp) { order_body(kp, kp.
 // in creation order).  Between steps the meshed slots are renumbered in
 // block order once the blocks created since the last renumbering reach
 // 1/16 of the meshed ones: k_sort_rank decides and ranks the blocks
-// (perm[new slot] = old slot, in cand_list, free between steps),
-// k_sort_move / k_sort_back move the populations of the next step's read
-// buffer through the other buffer (idle between steps), k_sort_aux does the
-// same for the solid words, the previous velocities, the 16-bit forms'
-// previous densities and block_of, and k_sort_tables
+// (perm[new slot] = old slot, in cand_list, free between steps), k_sort_aux
+// moves the solid words, the previous velocities, the 16-bit forms'
+// previous densities and block_of through the other population buffer
+// (idle between steps), k_sort_move / k_sort_back then move the populations
+// of the next step's read buffer through it, which leaves both buffers
+// holding them, and k_sort_tables
 // rebuilds the neighbour-slot table.  The launches after k_sort_rank return
 // at once when it decided not to move.  No cell's arithmetic changes: the
 // results are the same bit for bit.
@@ -3015,11 +3016,14 @@ struct Launch {
     }
     static cudaError_t sort(const KParams &kp, int sms, cudaStream_t s)
     {
+        // the other arrays first: the population move then leaves the same
+        // renumbered populations in both buffers (held cells of the FP32
+        // form are never rewritten and are read from either buffer)
         k_sort_rank<<<1, 1024, 0, s>>>(kp);
-        k_sort_move<ST><<<sms * 4, THREADS, 0, s>>>(kp);
-        k_sort_back<ST><<<sms * 4, THREADS, 0, s>>>(kp);
         k_sort_aux<ST, false><<<sms * 4, THREADS, 0, s>>>(kp);
         k_sort_aux<ST, true><<<sms * 4, THREADS, 0, s>>>(kp);
+        k_sort_move<ST><<<sms * 4, THREADS, 0, s>>>(kp);
+        k_sort_back<ST><<<sms * 4, THREADS, 0, s>>>(kp);
         k_sort_tables<<<sms * 2, THREADS, 0, s>>>(kp);
         return cudaGetLastError();
     }
