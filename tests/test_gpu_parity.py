@@ -193,13 +193,17 @@ def interior_meshed_blocks(gpu, case, count, seed=0):
     return picks
 
 
-def test_full_size_injection_sampled_one_step(L):
+@pytest.mark.parametrize("streaming", ["ab", "aa"])
+def test_full_size_injection_sampled_one_step(L, streaming):
     """256^3 porous injection in the benchmark's launch configuration: after
-    300 steps, one further step of sampled interior blocks equals the
-    oracle's step from the same populations; the meshed set stays connected."""
+    300 steps (slots renumbered in block order on the way, A-B), one further
+    step of sampled interior blocks equals the oracle's step from the same
+    populations; the meshed set stays connected."""
     case = W.porous_injection()
-    gpu = gpu_of(L, case)
+    gpu = gpu_of(L, case, streaming=streaming)
     gpu.step(300)
+    if streaming == "ab":
+        assert gpu.stats()["slot_sorts"] > 0
     picks = interior_meshed_blocks(gpu, case, 4)
     assert len(picks) >= 2
     one_step_sample(L, gpu, case, picks)
