@@ -283,8 +283,9 @@ int lbm_set_exec(lbm_ctx *ctx, int mode);
  * 0 = never) the device checks whether the blocks created since the last
  * renumbering reach 1/16 of the meshed ones and, if so, renumbers the meshed
  * slots in block order between two steps (moving the populations through
- * the idle population buffer; not with A-A streaming).  Results are the same
- * bit for bit with any period.  Errors: LBM_EINVAL (period < 0). */
+ * the idle population buffer; with A-A streaming, which has none, the
+ * passes visit the slots in block order instead).  Results are the same bit
+ * for bit with any period.  Errors: LBM_EINVAL (period < 0). */
 int lbm_set_slot_order(lbm_ctx *ctx, int period);
 
 /* Test hook of the bounded device wait: one cooperative launch whose grid

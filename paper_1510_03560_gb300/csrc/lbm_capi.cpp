@@ -405,11 +405,11 @@ int ensure_graph(lbm_ctx *c)
 }
 
 // Whether the slots may need renumbering in block order before step t (the
-// device decides whether they do; A-A streaming has no idle buffer to move
-// them through).
+// device decides whether they do; with A-A streaming, which has no idle
+// buffer to move them through, only the visiting order changes).
 bool sort_point(const lbm_ctx *c, int t)
 {
-    return c->sort_period > 0 && c->p.progressive && !c->kp.aa && t > 0 && t % c->sort_period == 0;
+    return c->sort_period > 0 && c->p.progressive && t > 0 && t % c->sort_period == 0;
 }
 
 int enqueue_steps(lbm_ctx *c, int nsteps)
@@ -420,7 +420,8 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
         if (sort_point(c, t)) {
             // the side stream reads the tables: let its last round finish
             if (c->mlp) CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->stream, c->side_done, 0));
-            CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return launch_sort(c->kp, c->sms, c->stream); }, 6));
+            CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return launch_sort(c->kp, c->sms, c->stream); },
+                                  c->kp.aa ? 1 : 6));
         }
         if (c->mlp && t % c->period == 0) {
             int rc = enqueue_proposer(c, t);
@@ -429,7 +430,7 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
         // steps up to the next proposer round or renumbering check
         int chunk = nsteps - k;
         if (c->mlp) chunk = std::min(chunk, c->period - t % c->period);
-        if (c->sort_period > 0 && c->p.progressive && !c->kp.aa)
+        if (c->sort_period > 0 && c->p.progressive)
             chunk = std::min(chunk, c->sort_period - t % c->sort_period);
         if (c->exec == LBM_EXEC_PERSISTENT) {
             CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] {
@@ -564,6 +565,7 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
         {(void **)&k.f, dev16 ? 0 : (aa ? 1 : 2) * one_buf * sizeof(float)},
         {(void **)&k.h, dev16 ? 2 * one_buf * sizeof(uint32_t) : 0},
         {(void **)&k.held_rank, aa ? (size_t)c->nblocks * sizeof(int) : 0},
+        {(void **)&k.order, aa ? (size_t)c->capacity * sizeof(int) : 0},
         {(void **)&k.mac, (dev16 ? 2 : 1) * (size_t)(c->capacity + 1) * CELLS * sizeof(float4)},
         {(void **)&k.nbits, (size_t)c->capacity * CELLS * sizeof(uint32_t)},
         {(void **)&k.nbr, (size_t)c->capacity * NBR_STRIDE * sizeof(int)},

@@ -51,6 +51,7 @@ struct Ctrl {
     unsigned long long sorted_created;  // `created` at the last renumbering of the slots
     unsigned long long sorts;           // renumberings of the slots in block order
     int sort_go;       // the renumbering under way moves the slots
+    int n_sorted;      // A-A: the first n_sorted work items visit kp.order
 };
 
 // Everything a kernel needs, passed by value.
@@ -115,6 +116,9 @@ struct KParams {
     float *held_f;          // [held blocks][2][Q][CELLS]: the constant
                             // populations of held cells (A-A only)
     const int *held_rank;   // [nblocks]: row of held_f, -1 without held cells
+    int *order;             // A-A: [capacity] slots in block order (the first
+                            // ctrl->n_sorted of them); the passes visit them
+                            // in this order instead of moving the blocks
 };
 
 // Kernel kinds for per-kernel timing.

@@ -1225,9 +1225,18 @@ __global__ void __launch_bounds__(1024) k_sort_rank(KParams kp)
     }
     __syncthreads();
     if (!go) return;
+    // A-A: no idle buffer to move the blocks through; the passes visit the
+    // slots in this order instead
+    int *perm = kp.aa ? kp.order : kp.cand_list;
     scan_blocks(
         kp.nbx * kp.nby * kp.nbz, [&](int b) { return kp.slot_of[b] >= 0; },
-        [&](int b, int r) { kp.cand_list[r] = kp.slot_of[b]; });
+        [&](int b, int r) { perm[r] = kp.slot_of[b]; });
+    if (kp.aa && threadIdx.x == 0) {
+        ctrl->n_sorted = n;
+        ctrl->sorted_created = ctrl->created;
+        ctrl->sorts += 1ull;
+        ctrl->sort_go = 0;
+    }
 }
 
 // dst[new][k] = src[perm[new]][k] over `words` words per slot, or a plain
@@ -1939,20 +1948,24 @@ __device__ __forceinline__ void macro_aa_body(const KParams &kp, int step, int c
     const int n = ctrl->n_active[par];
     if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
     const int total = n * PARTS;
+    const int ns = ctrl->n_sorted;  // work items below ns * PARTS visit kp.order
+    auto slot_of_item = [&](int i) { return i / PARTS < ns ? kp.order[i / PARTS] : i / PARTS; };
     int it = blockIdx.x;
-    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    int next_slot = it < total ? slot_of_item(it) : 0;
+    int next_row = it < total ? nbr_row_lane(kp, next_slot) : SOLIDBLK;
     uint32_t next_bits =
-        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+        it < total ? kp.nbits[(size_t)next_slot * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
     for (; it < total; it += gridDim.x) {
-        const int slot = it / PARTS;
+        const int slot = next_slot;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
         const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
         if (it2 < total) {
-            next_row = nbr_row_lane(kp, it2 / PARTS);
-            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+            next_slot = slot_of_item(it2);
+            next_row = nbr_row_lane(kp, next_slot);
+            next_bits = kp.nbits[(size_t)next_slot * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
         const bool live = !(bits & 1u);
         const bool held = (bits >> HELD_BIT) & 1u;
@@ -2003,20 +2016,24 @@ __device__ __forceinline__ void collide_aa_body(const KParams &kp, int step)
         ctrl->fluid_updates += ctrl->fluid_active;
     }
     const int total = n * PARTS;
+    const int ns = ctrl->n_sorted;  // work items below ns * PARTS visit kp.order
+    auto slot_of_item = [&](int i) { return i / PARTS < ns ? kp.order[i / PARTS] : i / PARTS; };
     int it = blockIdx.x;
-    int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    int next_slot = it < total ? slot_of_item(it) : 0;
+    int next_row = it < total ? nbr_row_lane(kp, next_slot) : SOLIDBLK;
     uint32_t next_bits =
-        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+        it < total ? kp.nbits[(size_t)next_slot * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
     for (; it < total; it += gridDim.x) {
-        const int slot = it / PARTS;
+        const int slot = next_slot;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
         const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
         const WarpNbr wn = warp_nbr_of(kp, next_row);
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
         if (it2 < total) {
-            next_row = nbr_row_lane(kp, it2 / PARTS);
-            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+            next_slot = slot_of_item(it2);
+            next_row = nbr_row_lane(kp, next_slot);
+            next_bits = kp.nbits[(size_t)next_slot * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
         const bool nonsolid = !(bits & 1u);
         const bool held = (bits >> HELD_BIT) & 1u;
@@ -3016,6 +3033,10 @@ struct Launch {
     }
     static cudaError_t sort(const KParams &kp, int sms, cudaStream_t s)
     {
+        if (kp.aa) {  // a new visiting order, no moves
+            k_sort_rank<<<1, 1024, 0, s>>>(kp);
+            return cudaGetLastError();
+        }
         // the other arrays first: the population move then leaves the same
         // renumbered populations in both buffers (held cells of the FP32
         // form are never rewritten and are read from either buffer)

@@ -33,13 +33,16 @@ def _state(sim, ids=None):
     return st
 
 
-@pytest.mark.parametrize("storage,mode", [("fp32", "stream"), ("fp16", "stream"), ("fp32", "graph"),
-                                          ("fp32", "persistent")])
-def test_renumbering_changes_nothing(L, storage, mode):
+@pytest.mark.parametrize("storage,mode,streaming", [("fp32", "stream", "ab"), ("fp16", "stream", "ab"),
+                                                    ("fp32", "graph", "ab"), ("fp32", "persistent", "ab"),
+                                                    ("fp32", "stream", "aa"), ("fp32", "graph", "aa")])
+def test_renumbering_changes_nothing(L, storage, mode, streaming):
+    """(A-A streaming renumbers the order in which the passes visit the
+    slots, not the slots.)"""
     case = _case()
     ref = L.from_case(case, storage=storage)
     ref.set_slot_order(0)
-    sim = L.from_case(case, storage=storage)
+    sim = L.from_case(case, storage=storage, streaming=streaming)
     sim.set_slot_order(4)
     sim.set_exec(mode)
     for n in (5, 11, 17, 31):
@@ -51,9 +54,13 @@ def test_renumbering_changes_nothing(L, storage, mode):
         for k in range(2):
             np.testing.assert_array_equal(a[1][k], b[1][k])
         np.testing.assert_array_equal(a[2], b[2])
-        if ids is not None:
-            for x, y in zip(a[3], b[3]):
-                np.testing.assert_array_equal(x, y)
+        if ids is not None:  # non-solid cells (solid cells' stored values are never read)
+            ct = case["cell_type"]
+            nbx, nby = ct.shape[2] // 8, ct.shape[1] // 8
+            for blk, x, y in zip(ids, a[3], b[3]):
+                bx, by, bz = blk % nbx, (blk // nbx) % nby, blk // (nbx * nby)
+                keep = ct[bz * 8:bz * 8 + 8, by * 8:by * 8 + 8, bx * 8:bx * 8 + 8].reshape(-1) != W.SOLID
+                np.testing.assert_array_equal(x[..., keep], y[..., keep])
     sorts = sim.stats()["slot_sorts"]
     print(f"{storage} {mode}: {sorts} renumberings, {len(sim.active_blocks())} meshed blocks")
     assert sorts > 0 and ref.stats()["slot_sorts"] == 0
