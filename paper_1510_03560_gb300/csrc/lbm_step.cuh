@@ -382,14 +382,21 @@ __device__ __forceinline__ void dev_issue(const KParams &kp, const WarpNbr &wn, 
     const bool held = (bits >> HELD_BIT) & 1u;
     const unsigned ambm = wn.amb | (own_ambient ? (1u << 13) : 0u);
     uint32_t off[Q];
-    uint32_t ambs = 0;
     Unroll<0, Q>::run([&]<int I>() {
         int k;
         off[I] = src_offset<I>(wn, own, lx, ly, lz, bits, held, k);
-        const bool bounce = (bits >> I) & 1u;
-        const bool a = (held || bounce) ? own_ambient : ((ambm >> k) & 1u);
-        ambs |= (uint32_t)a << I;
     });
+    // which populations come from the ambient state; none in a warp with
+    // no unmeshed neighbour block (most warps: the flags are skipped there)
+    uint32_t ambs = 0;
+    if (ambm != 0u) {  // warp-uniform
+        Unroll<0, Q>::run([&]<int I>() {
+            const int k = nbk(lx - cx(I), ly - cy(I), lz - cz(I));
+            const bool bounce = (bits >> I) & 1u;
+            const bool a = (held || bounce) ? own_ambient : ((ambm >> k) & 1u);
+            ambs |= (uint32_t)a << I;
+        });
+    }
     L.ambs = ambs;
     Unroll<0, Q>::run([&]<int I>() { L.v[I] = live ? __ldg(rd + off[I]) : 0u; });
 }
