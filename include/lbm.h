@@ -14,9 +14,10 @@
  *     Sec. 4.1-4.3, Fig. 4.
  *   - Throughput metric (MLUPS): Sec. 5.3, Eq. 16.
  *
- * The sub-domain (the unit of meshing) is an 8 x 8 x 8 block of cells.  A
- * block is "active" once meshed; blocks are never removed.  Unmeshed
- * blocks behave as a resting ambient at the densities rho_amb.
+ * The sub-domain (the unit of meshing) is a block of 512 cells, 8 x 8 x 8
+ * by default (lbm_params.block selects 16 x 8 x 4, 16 x 4 x 8 or
+ * 32 x 4 x 4).  A block is "active" once meshed; blocks are never removed.
+ * Unmeshed blocks behave as a resting ambient at the densities rho_amb.
  *
  * Conventions shared by every entry point:
  *   - Grid arrays are dense, x fastest: index x + nx * (y + ny * z).
@@ -25,7 +26,7 @@
  *   - Cell types: 0 fluid, 1 solid (halfway bounce-back wall), 2 held (its
  *     populations stay at the initial equilibrium: inlets, outlets).
  *   - Block ids are linear, x fastest: bx + nbx * (by + nby * bz), with
- *     nbx = nx / 8 and so on.
+ *     nbx = nx / (block extent along x) and so on.
  *   - Host pointers belong to the caller and are only read or written
  *     during the call; the library never keeps them.
  *   - The context owns all device memory it allocates (through the
@@ -87,7 +88,7 @@ extern "C" {
 #define LBM_STREAM_AB 0
 #define LBM_STREAM_AA 1
 
-#define LBM_BLOCK_EDGE 8 /* cells per block edge */
+#define LBM_BLOCK_EDGE 8 /* cells per block edge of the default 8^3 block */
 #define LBM_Q 19         /* D3Q19 populations per component */
 
 typedef struct lbm_ctx lbm_ctx;
@@ -218,9 +219,10 @@ int lbm_mass(lbm_ctx *ctx, double *mass);
 
 /* Post-collision populations of one meshed block, host array
  * [ncomp][19][512] in the library's velocity order (lbm_velocities), cell
- * index x + 8 * (y + 8 * z) within the block; in the 16-bit storage forms
- * the stored deviations with their reference added back, in FP32, and 0 at
- * solid cells.  LBM_EINVAL if the block is not meshed. */
+ * index x + bx * (y + by * z) within a bx x by x bz block; in the 16-bit
+ * storage forms the stored deviations with their reference added back, in
+ * FP32, and 0 at solid cells (A-A streaming: 0 at solid cells as well).
+ * LBM_EINVAL if the block is not meshed. */
 int lbm_get_block_populations(lbm_ctx *ctx, int32_t block_id, float *out);
 
 /* The library's D3Q19 velocity order: e[3 * i + axis], 19 x 3 ints. */
