@@ -89,7 +89,7 @@ __device__ __forceinline__ void step_done(Ctrl *ctrl, int step)
 constexpr int THREADS = 256;            // threads per CTA of the cell kernels
 // resident CTAs per SM the deviation-form step kernels are compiled for
 // (fewer registers would spill)
-constexpr int DEV_MACRO_MIN_CTAS = 3;
+constexpr int DEV_MACRO_MIN_CTAS = 2;
 constexpr int DEV_COLLIDE_MIN_CTAS = 2;
 constexpr int PARTS = CELLS / THREADS;  // CTA work items per block
 
@@ -1829,7 +1829,7 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
     }
 }
 
-__global__ void __launch_bounds__(THREADS, 4) k_macro2(KParams kp, int criterion)
+__global__ void __launch_bounds__(THREADS, 3) k_macro2(KParams kp, int criterion)
 {
     macro2_body(kp, kp.ctrl->step, criterion);
 }
@@ -1934,7 +1934,7 @@ __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
 }
 
 template <bool TAU1>
-__global__ void __launch_bounds__(THREADS) k_collide2(KParams kp)
+__global__ void __launch_bounds__(THREADS, 2) k_collide2(KParams kp)
 {
     const int step = *(volatile const int *)&kp.ctrl->step;
     collide2_body<TAU1>(kp, step);
