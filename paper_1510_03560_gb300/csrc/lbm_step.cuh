@@ -2814,7 +2814,7 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned expect, long long
 // The phases of one storage form and component count.
 template <int NC, bool TAU1, int ST>
 struct Phases {
-    static constexpr int MIN_CTAS = Store<ST>::DEV ? DEV_COLLIDE_MIN_CTAS : 3;
+    static constexpr int MIN_CTAS = Store<ST>::DEV ? DEV_COLLIDE_MIN_CTAS : 2;
     __device__ __forceinline__ static void macro(const KParams &kp, int step, int crit)
     {
         if constexpr (Store<ST>::DEV)
