@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -48,17 +49,25 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def kernel_code_hash(text):
+    """sha256 of kernel source without its // comments, trailing blanks and
+    empty lines: changes with the code, not with its comments."""
+    lines = (re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines())
+    return hashlib.sha256("\n".join(line for line in lines if line).encode()).hexdigest()
+
+
 def kernel_traffic(storage):
     """ncu DRAM bytes per meshed cell of the force+collide kernel in one
     storage form, if the committed capture was taken on the current kernel
-    source."""
+    code."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_1510_03560_gb300", "csrc", "lbm_step.cuh")
     try:
         with open(path) as fh:
             d = json.load(fh)
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if d.get("kernels_sha256") == h:
+        with open(src) as fh:
+            h = kernel_code_hash(fh.read())
+        if d.get("kernels_code_sha256") == h:
             return float(d["forms"][storage]["collide_dram_bytes_per_cell"])
     except Exception:
         pass

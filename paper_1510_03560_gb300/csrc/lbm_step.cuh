@@ -33,13 +33,19 @@
 // and hands them out with shuffles, and reads the per-cell solid bits
 // instead of block masks.
 //
-// One time step is three launches:
+// One time step is these launches:
 //   k_macro    pull streaming + Eqs. 4-5 + Eqs. 6-7 -> mac; criterion of
 //              Eq. 13 at cells bordering unmeshed blocks, marking targets
+//   k_order    the step's candidates renumbered in block order
 //   k_activate new blocks: slots, ambient equilibrium, their k_macro work
 //   k_collide  pull streaming again + forces (Eqs. 8-9, gravity,
 //              adhesion) from the neighbours' mac + forced BGK collision
 //              (Eqs. 10-12) -> f of the other buffer
+// Between steps, now and then, the k_sort_* launches renumber the meshed
+// slots in block order (locality; "slot order" below).  Further sections:
+// A-A streaming (one population array, Sec. 3), the TMA-staged and
+// deviation-form kernels, the cooperative multi-step kernel.  The file is
+// compiled once per storage form and, for FP32, once per block shape.
 #pragma once
 
 #include <climits>

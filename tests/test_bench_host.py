@@ -56,3 +56,14 @@ def test_reference_arm_other_ranks_exit(monkeypatch, capsys):
     args = argparse.Namespace(gpus=2, steps=5, warmup=3)
     assert bench.reference_arm(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_kernel_code_hash_follows_code_not_comments():
+    """The roofline traffic is kept only while the kernel code is the one the
+    ncu capture measured; comments and blank lines do not count."""
+    import bench
+    src = "int a = 1;  // one\n\n// note\nint b = a + 2;\n"
+    same = "int a = 1;\n// another note\nint b = a + 2;   \n"
+    changed = "int a = 1;\nint b = a + 3;\n"
+    assert bench.kernel_code_hash(src) == bench.kernel_code_hash(same)
+    assert bench.kernel_code_hash(src) != bench.kernel_code_hash(changed)
