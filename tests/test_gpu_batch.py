@@ -24,12 +24,16 @@ def _cases():
             W.droplet_impact(n=(32, 32, 48), seed=3), W.porous_injection(n=(32, 32, 32), seed=4, inlet=8, x_free=4)]
 
 
-@pytest.mark.parametrize("mode", ["stream", "graph", "persistent"])
-def test_batch_members_match_solo_runs(L, mode):
+@pytest.mark.parametrize("mode,slot_order", [("stream", 64), ("graph", 64), ("persistent", 64),
+                                             ("stream", 8)])
+def test_batch_members_match_solo_runs(L, mode, slot_order):
+    """(slot_order 8: the batch's slots are renumbered in block order several
+    times on the way; the solo runs keep the default.)"""
     cases = _cases()
     batch, place = B.pack(cases, width=96)
     sim = L.from_case(batch)
     sim.set_exec(mode)
+    sim.set_slot_order(slot_order)
     sim.step(60)
     fields = [B.split(np.stack(sim.macro(a)), place) for a in range(2)]
     act = set(sim.active_blocks().tolist())
@@ -42,6 +46,8 @@ def test_batch_members_match_solo_runs(L, mode):
         mine = np.array(sorted(i for i, b in enumerate(ids) if int(b) in act))
         np.testing.assert_array_equal(mine, solo.active_blocks())
         solo.close()
+    if slot_order == 8:
+        assert sim.stats()["slot_sorts"] > 0
     sim.close()
 
 
