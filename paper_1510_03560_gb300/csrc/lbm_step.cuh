@@ -1817,6 +1817,17 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
         const bool live = !(bits & 1u);
         const bool held = (bits >> HELD_BIT) & 1u;
         if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
+        if (!criterion || wn.amb == 0u) {
+            // warp-uniform: no cell of the warp borders an unmeshed block, so
+            // the criterion has nothing to test and only the densities are
+            // needed (summed in the same order as Moments2)
+            float2 rho = make_float2(0.f, 0.f);
+            pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live,
+                      [&]<int I>(float2 v) { rho = add2(rho, v); });
+            kp.mac[(size_t)slot * CELLS + c] =
+                live ? mac_pack(rho.x, psi_of(kp, rho.x), rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         Moments2 m;
         pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live,
                   [&]<int I>(float2 v) { m.template add<I>(v); });
@@ -1831,7 +1842,7 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
         // solid cells write zeros too (never read): complete sectors
         kp.mac[(size_t)slot * CELLS + c] =
             live ? mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (criterion) criterion_mark<2>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
+        criterion_mark<2>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
     }
 }
 
