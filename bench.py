@@ -5,14 +5,20 @@ GB300 (replicas on N GPUs under torchrun).
 Workload: 256^3 liquid injection into a gas-filled porous box (seeded
 spheres, radius 6-12, solid fraction 0.30, 64^2 inlet at u = 0.02, wetting
 g_ads = -0.2, Peng-Robinson component + ideal-gas component), 5000 time
-steps in total: W untimed warm-up steps from the initial state, then K timed
-steps.  A "step" is one time step of the whole hot path (streaming,
+steps in total, during which the meshed fraction grows from about 1 % to
+about 60 %.  A "step" is one time step of the whole hot path (streaming,
 moments, criterion and block creation, forces, collision).
 
+Every run goes through the whole 5000-step trajectory: W untimed warm-up
+steps, then K timed steps spread evenly over the remaining steps (the
+centres of K equal stretches), the steps between them untimed.  So the K
+timed steps sample the whole run, early and late, whatever K is.
+
 Timing: every timed step is bracketed by CUDA events on the library's
-stream; before each one a 256 MiB buffer is written to flush the 129 MB
-L2, outside the events.  MLUPS counts 512 cells for every meshed block of
-every timed step (Eq. 16 with the meshed cells as the domain).
+stream, with a synchronize before it and after it; before each one a
+256 MiB buffer is written to flush the 129 MB L2, outside the events.
+MLUPS counts 512 cells for every meshed block of every timed step (Eq. 16
+with the meshed cells as the domain).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -56,10 +62,10 @@ def kernel_code_hash(text):
     return hashlib.sha256("\n".join(line for line in lines if line).encode()).hexdigest()
 
 
-def kernel_traffic(storage):
-    """ncu DRAM bytes per meshed cell of the force+collide kernel in one
-    storage form, if the committed capture was taken on the current kernel
-    code."""
+def kernel_traffic(storage, which="collide"):
+    """ncu DRAM bytes per fluid cell of one storage form's kernel ("fused",
+    "collide") or of a whole step ("step"), if the committed capture was
+    taken on the current kernel code."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_1510_03560_gb300", "csrc", "lbm_step.cuh")
     try:
@@ -68,7 +74,7 @@ def kernel_traffic(storage):
         with open(src) as fh:
             h = kernel_code_hash(fh.read())
         if d.get("kernels_code_sha256") == h:
-            return float(d["forms"][storage]["collide_dram_bytes_per_cell"])
+            return float(d["forms"][storage][which + "_dram_bytes_per_fluid_cell"])
     except Exception:
         pass
     return None
@@ -164,9 +170,23 @@ def make_case(S=None, size=256, workload="injection", block="8x8x8"):
     return W.porous_injection(**kw)
 
 
-def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="fp32", proposer=None,
+TOTAL_STEPS = 5000  # the workload's run length
+
+
+def sample_steps(total, warmup, k):
+    """k step indices spread evenly over [warmup, total): the centres of k
+    equal stretches."""
+    span = total - warmup
+    if k > span:
+        raise ValueError(f"{k} timed steps do not fit in {span} steps after the warm-up")
+    return [warmup + (2 * i + 1) * span // (2 * k) for i in range(k)]
+
+
+def run_timed(L, torch, case, sample, total, progressive, flush, uuid, storage="fp32", proposer=None,
               exec_mode="stream", streaming="ab", slot_order=64):
-    """Warm up, then time `steps` steps one by one (L2 flushed before each).
+    """Run the whole trajectory of `total` steps, timing the steps listed in
+    `sample` one by one (L2 flushed before each, a synchronize on both
+    sides); the device time of the whole trajectory is recorded too.
     proposer: an lbm MLP to run the activation proposer with (period 16,
     threshold 0.5).  streaming: "ab" or "aa" (one population array)."""
     sim = L.from_case(case, progressive=progressive, storage=storage, streaming=streaming)
@@ -174,41 +194,62 @@ def run_timed(L, torch, case, warmup, steps, progressive, flush, uuid, storage="
     sim.set_slot_order(slot_order)
     if proposer is not None:
         sim.set_proposer(proposer, period=16, threshold=0.5)
-    sim.step(warmup)
     stream = torch.cuda.current_stream()
-    st0 = sim.stats()
-    sim.set_profiling(True)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    timed, untimed, per_step = [], [], []
+    acc = dict(cells=0, fluid=0, launches=0, created=0, prepared=0, prepared_hits=0,
+               kernel_ms=[0.0] * 4, kernel_launches=[0] * 4)
+    t = 0
     torch.cuda.synchronize()
     with ClockSampler(uuid) as clk:
-        for k in range(steps):
+        for s in list(sample) + [total]:
+            if s > t:  # untimed stretch (device time kept for the trajectory figure)
+                a, b = ev(), ev()
+                a.record(stream)
+                sim.step_async(s - t)
+                b.record(stream)
+                untimed.append((a, b))
+                t = s
+            if s >= total:
+                break
+            st0 = sim.stats()  # (synchronizes)
+            sim.set_profiling(True)
             flush.zero_()
-            starts[k].record(stream)
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
             sim.step_async(1)
-            ends[k].record(stream)
+            b.record(stream)
+            sim.sync()
+            torch.cuda.synchronize()
+            sim.set_profiling(False)
+            st1 = sim.stats()
+            t += 1
+            timed.append((a, b))
+            d = {k: st1[k] - st0[k] for k in ("cell_updates", "fluid_updates", "launches")}
+            acc["cells"] += d["cell_updates"]
+            acc["fluid"] += d["fluid_updates"]
+            acc["launches"] += d["launches"]
+            acc["created"] += st1["created_blocks"] - st0["created_blocks"]
+            acc["prepared"] += st1["prepared_blocks"] - st0["prepared_blocks"]
+            acc["prepared_hits"] += st1["prepared_hits"] - st0["prepared_hits"]
+            for k in range(4):
+                acc["kernel_ms"][k] += st1["kernel_ms"][k] - st0["kernel_ms"][k]
+                acc["kernel_launches"][k] += st1["kernel_launches"][k] - st0["kernel_launches"][k]
+            ms = a.elapsed_time(b)
+            per_step.append([s, round(d["cell_updates"] / 512 / st1["total_blocks"], 4), round(ms, 4),
+                             round(d["cell_updates"] / (ms * 1e-3) / 1e6, 1)])
         sim.sync()
         torch.cuda.synchronize()
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    st1 = sim.stats()
-    sim.set_profiling(False)
-    out = dict(
-        ms=ms,
-        cells=st1["cell_updates"] - st0["cell_updates"],
-        fluid=st1["fluid_updates"] - st0["fluid_updates"],
-        launches=st1["launches"] - st0["launches"],
-        kernel_ms=[b - a for a, b in zip(st0["kernel_ms"], st1["kernel_ms"])],
-        kernel_launches=[b - a for a, b in zip(st0["kernel_launches"], st1["kernel_launches"])],
-        active_end=st1["active_blocks"],
-        created=st1["created_blocks"] - st0["created_blocks"],
-        prepared=st1["prepared_blocks"] - st0["prepared_blocks"],
-        prepared_hits=st1["prepared_hits"] - st0["prepared_hits"],
-        nonsolid_blocks=st1["nonsolid_blocks"],
-        total_blocks=st1["total_blocks"],
-        device_bytes=st1["device_bytes"],
-        slot_sorts=st1["slot_sorts"],
-        clocks=clk.summary(),
-    )
+    st = sim.stats()
+    ms = sum(a.elapsed_time(b) for a, b in timed)
+    traj_ms = ms + sum(a.elapsed_time(b) for a, b in untimed)
+    out = dict(acc, ms=ms, per_step=per_step, traj_ms=traj_ms, traj_cells=st["cell_updates"],
+               active_end=st["active_blocks"], nonsolid_blocks=st["nonsolid_blocks"],
+               total_blocks=st["total_blocks"], device_bytes=st["device_bytes"],
+               slot_sorts=st["slot_sorts"], fused_deferred=st["fused_deferred"],
+               fused_waited=st["fused_waited"], fused_lag_distance=st["fused_lag_distance"],
+               clocks=clk.summary())
     sim.close()
     return out
 
@@ -249,6 +290,22 @@ def oracle_sample(budget_s=15.0, max_steps=None):
         steps += 1
     sim.close()
     return dict(mlups=cells / t_used / 1e6, steps=steps, seconds=t_used, cores=O.threads())
+
+
+def oracle_sample_single_thread(budget_s=8.0):
+    """oracle_sample with one OpenMP thread, in a fresh interpreter (the
+    thread count is fixed when the oracle library loads)."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(budget_s=%r)))" % (ROOT, budget_s))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                           timeout=budget_s * 6 + 60)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+    return {"value": round(d["mlups"], 4), "unit": "MLUPS", "cores": d["cores"],
+            "sample": f"{CPU_SAMPLE}, {d['steps']} steps, {d['seconds']:.1f} s"}
 
 
 def dist_setup():
@@ -374,8 +431,13 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4950)
-    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20,
+                    help="timed steps, spread evenly over the trajectory after the warm-up")
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--total", type=int, default=TOTAL_STEPS,
+                    help="length of the trajectory every run goes through (the workload's 5000 steps)")
+    ap.add_argument("--fusion", default="off", choices=["on", "off"],
+                    help="collision and the next step's pass 1 in one launch (FP32, two components, A-B)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--S", type=float, default=None, help="criterion threshold override")
     ap.add_argument("--no-static", action="store_true")
@@ -422,20 +484,22 @@ def main():
     from paper_1510_03560_gb300 import lbm as L
     uuid = device_uuid(torch, local)
     case = make_case(args.S, args.size, args.workload, args.block)
+    case["params"]["fusion"] = (args.fusion == "on", 0)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    sample = sample_steps(args.total, args.warmup, args.steps)
     if args.static_only:
-        st = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage,
+        st = run_timed(L, torch, case, sample, args.total, 0, flush, uuid, args.storage,
                        exec_mode=args.exec, streaming=args.streaming)
         if rank == 0:
             print(json.dumps({"static_mlups": st["cells"] / (st["ms"] * 1e-3) / 1e6,
                               "ms": st["ms"], "kernel_ms": st["kernel_ms"],
-                              "kernel_launches": st["kernel_launches"]}), flush=True)
+                              "kernel_launches": st["kernel_launches"], "fusion": args.fusion}), flush=True)
         return 0
 
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    prog = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, args.storage,
+    prog = run_timed(L, torch, case, sample, args.total, 1, flush, uuid, args.storage,
                      exec_mode=args.exec, streaming=args.streaming, slot_order=args.slot_order)
     torch.cuda.synchronize()
     if dist is not None:
@@ -444,37 +508,42 @@ def main():
 
     stat = None
     if not args.no_static:
-        stat = run_timed(L, torch, case, args.warmup, args.steps, 0, flush, uuid, args.storage,
+        stat = run_timed(L, torch, case, sample, args.total, 0, flush, uuid, args.storage,
                          streaming=args.streaming)
         s_max, s_cells = reduce_max_sum(dist, torch, stat["ms"], stat["cells"])
     forms = {}
+
+    def form_line(r, **extra):
+        f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
+        d = {"mlups": round(f_cells / (f_max * 1e-3) / 1e6, 1),
+             "fluid_mlups": round(r["fluid"] / (r["ms"] * 1e-3) / 1e6, 1),
+             "active_fraction_end": round(r["active_end"] / r["total_blocks"], 4),
+             "collide_ms_per_step": round(r["kernel_ms"][2] / args.steps, 5)}
+        d.update(extra)
+        return d
+
     if not args.no_forms and args.storage == "fp32" and args.streaming == "ab":
         from paper_1510_03560_gb300 import proposer as PR
-        r = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, "fp32", streaming="aa")
-        f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
-        forms["aa"] = {"mlups": round(f_cells / (f_max * 1e-3) / 1e6, 1),
-                       "collide_ms_per_step": round(r["kernel_ms"][2] / args.steps, 5),
-                       "macro_ms_per_step": round(r["kernel_ms"][0] / args.steps, 5),
-                       "device_bytes": r["device_bytes"], "device_bytes_ab": prog["device_bytes"],
-                       "streaming": "A-A: one population array updated in place"}
+        r = run_timed(L, torch, case, sample, args.total, 1, flush, uuid, "fp32", streaming="aa")
+        forms["aa"] = form_line(r, macro_ms_per_step=round(r["kernel_ms"][0] / args.steps, 5),
+                                device_bytes=r["device_bytes"], device_bytes_ab=prog["device_bytes"],
+                                streaming="A-A: one population array updated in place")
         for form in ("fp16", "bf16"):
-            r = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, form)
-            f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
-            forms[form] = {"mlups": round(f_cells / (f_max * 1e-3) / 1e6, 1),
-                           "active_fraction_end": round(r["active_end"] / r["total_blocks"], 4),
-                           "collide_ms_per_step": round(r["kernel_ms"][2] / args.steps, 5)}
+            r = run_timed(L, torch, case, sample, args.total, 1, flush, uuid, form)
+            forms[form] = form_line(r)
+            if not args.no_static:
+                # the same kernels on the same (static) cells as the FP32 static arm
+                r = run_timed(L, torch, case, sample, args.total, 0, flush, uuid, form)
+                forms[form + "_static"] = form_line(r)
         mlp = PR.load_model(L)
-        r = run_timed(L, torch, case, args.warmup, args.steps, 1, flush, uuid, "fp32", proposer=mlp)
-        f_max, f_cells = reduce_max_sum(dist, torch, r["ms"], r["cells"])
-        forms["learned"] = {
-            "mlups": round(f_cells / (f_max * 1e-3) / 1e6, 1),
-            "created": r["created"], "prepared": r["prepared"], "prepared_hits": r["prepared_hits"],
-            "activate_ms_per_step": round(r["kernel_ms"][1] / args.steps, 5),
-            "activate_ms_per_step_without": round(prog["kernel_ms"][1] / args.steps, 5),
-            "period": 16, "threshold": 0.5, "inference": "bf16 operands, fp32 accumulation"}
+        r = run_timed(L, torch, case, sample, args.total, 1, flush, uuid, "fp32", proposer=mlp)
+        forms["learned"] = form_line(
+            r, created=r["created"], prepared=r["prepared"], prepared_hits=r["prepared_hits"],
+            activate_ms_per_step=round(r["kernel_ms"][1] / args.steps, 5),
+            activate_ms_per_step_without=round(prog["kernel_ms"][1] / args.steps, 5),
+            period=16, threshold=0.5, inference="bf16 operands, fp32 accumulation")
         mlp.close()
-    e2e = None if args.no_e2e else run_e2e(L, torch, case, args.warmup + args.steps, args.storage,
-                                           args.streaming)
+    e2e = None if args.no_e2e else run_e2e(L, torch, case, args.total, args.storage, args.streaming)
     if e2e is not None:
         e_max, e_cells = reduce_max_sum(dist, torch, e2e["wall"], e2e["cells"])
 
@@ -489,23 +558,30 @@ def main():
     # algorithmic bytes: 304 B for every fluid cell updated (solid cells move
     # no data, held cells are read by their neighbours but never written)
     step_frac = prog["fluid"] * bpu / (prog["ms"] * 1e-3) / 1e9 / peak
-    # dominant kernel: force + collide (kind 2)
+    # dominant kernel: the collision launch (kind 2); fused, it also runs the
+    # next step's pass 1, so its algorithmic bytes are the whole step's
+    fused = args.fusion == "on" and args.storage == "fp32" and args.streaming == "ab" and \
+        args.exec in ("stream", "graph")
     kms, kn = prog["kernel_ms"][2], prog["kernel_launches"][2]
     coll_gbs = prog["fluid"] * bpu / (kms * 1e-3) / 1e9 if kms > 0 else None
-    traffic_pc = kernel_traffic(args.storage) if args.streaming == "ab" else None
+    traffic_pc = kernel_traffic(args.storage, "fused" if fused else "collide") if args.streaming == "ab" else None
     avg_cells = prog["cells"] / max(kn, 1)
     avg_fluid = prog["fluid"] / max(kn, 1)
     roofline = {
         "bound": "hbm", "achieved": round(coll_gbs, 1) if coll_gbs else None,
         "peak": peak, "unit": "GB/s",
         "frac": round(coll_gbs / peak, 4) if coll_gbs else None,
-        "traffic": round(traffic_pc * avg_cells) if traffic_pc else None,
-        "kernel": ("k_collide (force gather + exact-difference collision + pull streaming)"
+        "traffic": round(traffic_pc * avg_fluid) if traffic_pc else None,
+        "kernel": ("k_fused2 (collision of step t: pull, force gather, exact-difference collision; "
+                   "pass 1 of step t+1: pull, densities, psi, criterion)" if fused else
+                   "k_collide (force gather + exact-difference collision + pull streaming)"
                    if args.streaming == "ab" else
                    "k_collide_aa (force gather + exact-difference collision, A-A in place)"),
         "peak_kind": peak_kind,
         "algorithmic_bytes_per_launch": round(avg_fluid * bpu),
         "avg_launch_ms": round(kms / max(kn, 1), 5),
+        "traffic_basis": "ncu dram bytes per fluid cell of the kernel (profiles/traffic.json) x "
+                         "the launch's fluid cells",
     }
     share = {name: round(v / max(sum(prog["kernel_ms"]), 1e-9), 4)
              for name, v in zip(("macro", "activate", "collide", "other"), prog["kernel_ms"])}
@@ -515,16 +591,26 @@ def main():
                      ).replace("8^3 blocks", "8^3 blocks" if args.block == "8x8x8" else f"{args.block} blocks"),
         "mode": "progressive", "grid": [case["params"][k] for k in ("nx", "ny", "nz")],
         "block": list(case["params"]["block"]),
-        "storage": args.storage, "exec": args.exec, "streaming": args.streaming,
+        "storage": args.storage, "exec": args.exec, "streaming": args.streaming, "fusion": args.fusion,
         "slot_order_period": args.slot_order, "slot_sorts": prog["slot_sorts"],
-        "S": case["params"]["S"], "timed_steps": [args.warmup, args.warmup + args.steps],
+        "S": case["params"]["S"],
+        "trajectory_steps": args.total, "timed_steps": sample,
+        "timing": f"{args.steps} steps spread evenly over steps {args.warmup}..{args.total - 1} of the "
+                  f"{args.total}-step trajectory (the rest run untimed)",
+        "samples": {"columns": ["step", "meshed_fraction", "ms", "mlups"], "rows": prog["per_step"]},
         "active_fraction_end": round(prog["active_end"] / prog["total_blocks"], 4),
         "mean_active_fraction": round(prog["cells"] / 512 / args.steps / prog["total_blocks"], 4),
+        "trajectory_mlups": round(prog["traj_cells"] / (prog["traj_ms"] * 1e-3) / 1e6, 1),
         "step_hbm_frac": round(step_frac, 4), "kernel_time_share": share,
         "fluid_mlups": round(prog["fluid"] / (prog["ms"] * 1e-3) / 1e6, 1),
+        "fused_deferred_items": prog["fused_deferred"], "fused_waited_items": prog["fused_waited"],
+        "fused_lag_distance": prog["fused_lag_distance"],
         "l2": "256 MiB buffer written before every timed step; flush outside the timed events",
         "parallelism": f"replicas x{world}",
     }
+    step_traffic = kernel_traffic(args.storage, "step") if args.streaming == "ab" else None
+    if step_traffic:
+        config["step_dram_bytes_per_fluid_cell"] = step_traffic
     if forms:
         forms["fp32_progressive_mlups"] = round(mlups, 1)
         config["forms"] = forms
@@ -540,6 +626,9 @@ def main():
         cpu = {"value": round(r["mlups"], 4), "unit": "MLUPS", "cores": r["cores"],
                "kind": "oracle",
                "sample": f"{CPU_SAMPLE}, {r['steps']} steps, {r['seconds']:.1f} s"}
+        one = oracle_sample_single_thread(budget_s=8.0)
+        if one is not None:
+            cpu["single_thread"] = one
     line = {
         "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 5),

@@ -55,7 +55,9 @@ extern "C" {
 
 /* How lbm_step enqueues the steps (lbm_set_exec); every mode runs the same
  * per-cell code and gives the same results bit for bit. */
-#define LBM_EXEC_STREAM 0     /* three launches per step (default) */
+#define LBM_EXEC_STREAM 0     /* one launch per step for pass 1, one for the collision
+                                 (or one for both, fused: lbm_set_fusion), plus block
+                                 creation's two (default) */
 #define LBM_EXEC_GRAPH 1      /* the launches of two steps captured once as a CUDA graph,
                                  replayed (the kernels read the step count on the device) */
 #define LBM_EXEC_PERSISTENT 2 /* the steps of a call in one cooperative launch, with grid
@@ -149,6 +151,12 @@ typedef struct lbm_stats {
     long long prepared_blocks;  /* blocks the activation proposer prepared */
     long long prepared_hits;    /* created blocks that had been prepared */
     long long slot_sorts;       /* renumberings of the meshed slots in block order */
+    long long fused_deferred;   /* fused step: pass-1 work items deferred to the end of
+                                   their launch (their neighbourhood's collisions came
+                                   later in the work order), summed over launches */
+    long long fused_waited;     /* fused step: pass-1 items that found a neighbouring
+                                   collision still running and waited for it */
+    long long fused_lag_distance; /* fused step: the slot distance its lag covers now */
 } lbm_stats;
 
 /* Validate `p`, allocate the block pool (capacity x 2 buffers x ncomp x 19 x
@@ -289,6 +297,37 @@ int lbm_set_exec(lbm_ctx *ctx, int mode);
  * passes visit the slots in block order instead).  Results are the same bit
  * for bit with any period.  Errors: LBM_EINVAL (period < 0). */
 int lbm_set_slot_order(lbm_ctx *ctx, int period);
+
+/* Slot order of the block pool: the meshed slots are numbered in strips of
+ * `rows` block rows along y, each strip in z, then y, then x order (0 = plain
+ * block order, bx fastest; -1 = automatic, the default: strips of about 512
+ * blocks per z layer, or block order when the grid is narrower).  A strip
+ * keeps a block's z neighbours about rows * nbx slots away instead of
+ * nbx * nby, so that the fused step's two passes meet within L2.  Applies at
+ * the next lbm_set_geometry and at every renumbering.  Results are the same
+ * bit for bit in every order.  Errors: LBM_EINVAL (rows < -1). */
+int lbm_set_slot_strip(lbm_ctx *ctx, int rows);
+
+/* Fused step (FP32 storage, two components, A-B streaming, STREAM and GRAPH
+ * modes; off by default: on one GB300 it moves about 20 % fewer HBM bytes per
+ * step but runs slower, pass 1 running at the collision's register budget).  The paper's step (Sec. 2, Eqs. 4-12) needs psi of
+ * the 18 neighbours from the current step (Eqs. 6-9), so it is computed in
+ * two passes over the meshed blocks: pass 1 streams the populations (Eq. 10,
+ * left-hand side) for the densities, psi and the criterion (Eq. 13), pass 2
+ * streams them again for the forces and the collision.  Fused, one launch
+ * runs the collision of step t and, a lag behind it in the same work order,
+ * pass 1 of step t + 1, which then reads the populations just written from
+ * L2 rather than from HBM.  Pass 1 of a block waits (bounded; LBM_ETIMEOUT)
+ * until the collisions of its 26 neighbours are written, or is deferred to
+ * the end of the launch when one of them comes later in the work order.  The
+ * results are the same bit for bit as unfused.  Between calls the next
+ * step's pass 1 may already have run: lbm_get_macro, lbm_mass and the other
+ * queries are unaffected.
+ *   on       1 fused, 0 two launches per step
+ *   max_lag  largest lag in half-block work items (0 = the default, 1536);
+ *            below the neighbours' slot distance, more items are deferred
+ * Errors: LBM_EINVAL (on not 0 or 1, max_lag < 0). */
+int lbm_set_fusion(lbm_ctx *ctx, int on, int max_lag);
 
 /* Test hook of the bounded device wait: one cooperative launch whose grid
  * barrier expects `missing` more CTAs than it has, polling at most `spins`

@@ -98,6 +98,13 @@ struct lbm_ctx {
     cudaStream_t cap = nullptr;        // capture stream of the step graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;   // two steps
+    bool graph_fused = false;          // the graph holds fused launches
+    // fused step: the collision of step t and pass 1 of step t + 1 in one
+    // launch (FP32, two components, A-B, STREAM and GRAPH modes)
+    bool fuse = false;
+    bool ahead = false;  // pass 1 (with the criterion) of the next step has run
+    bool fz_clean = false;  // the arrival counters are set for the next fused launch
+    int strip_rows = -1; // slot order: -1 automatic, 0 block order, > 0 strip rows
 };
 
 namespace {
@@ -335,6 +342,53 @@ cudaError_t timed(lbm_ctx *c, int kind, F &&fn, int kernels = 1)
 
 int persistent_grid(lbm_ctx *c) { return c->sms * c->ctas_per_sm; }
 
+// Bytes of the fused step's arrival counters: two step parities of one int
+// per half block of the pool.
+size_t cflag_bytes(int capacity) { return (size_t)2 * capacity * 2 * sizeof(int); }
+
+// The fused launch counts arrivals in one parity of its counters and clears
+// the other for the next fused launch; any other step breaks that chain, so
+// both parities are cleared before the next fused launch.
+cudaError_t fused_launch(lbm_ctx *c, cudaStream_t s)
+{
+    if (!c->fz_clean) {
+        cudaError_t e = cudaMemsetAsync(c->kp.cflag, 0, cflag_bytes(c->capacity), s);
+        if (e != cudaSuccess) return e;
+        c->fz_clean = true;
+    }
+    return launch_fused(c->kp, c->sms, s);
+}
+
+// Strip height of the automatic slot order: about STRIP_BLOCKS blocks per
+// strip layer (0: the grid is narrow enough for plain block order).
+constexpr int STRIP_BLOCKS = 512;
+int auto_strip(int nbx, int nby)
+{
+    const int rows = std::max(1, STRIP_BLOCKS / std::max(nbx, 1));
+    return rows >= nby ? 0 : rows;
+}
+
+// The neighbour distance that covers FZ_COVER_PERMIL per mille of the slots
+// (as k_sort_tables computes it on the device), from the host's rows.
+int lag_distance(const std::vector<int> &rows, int n)
+{
+    if (n <= 0) return 0;
+    std::vector<long long> hist(FZ_BINS, 0);
+    for (int s = 0; s < n; ++s) {
+        int far = s;
+        for (int k = 0; k < NBR_STRIDE; ++k) far = std::max(far, rows[(size_t)s * NBR_STRIDE + k]);
+        hist[std::min((far - s) / FZ_BIN, FZ_BINS - 1)] += 1;
+    }
+    const long long need = ((long long)n * FZ_COVER_PERMIL + 999) / 1000;
+    long long cum = 0;
+    int b = 0;
+    for (; b < FZ_BINS - 1; ++b) {
+        cum += hist[b];
+        if (cum >= need) break;
+    }
+    return (b + 1) * FZ_BIN;
+}
+
 // Read the device control words after the stream is idle.
 int read_ctrl(lbm_ctx *c, Ctrl &out)
 {
@@ -375,23 +429,34 @@ void drop_graph(lbm_ctx *c)
     c->graph = nullptr;
 }
 
-// The launches of one step on stream s.
-cudaError_t launch_step(lbm_ctx *c, cudaStream_t s)
+// The launches of one step on stream s.  Fused: the step's pass 1 has run
+// ahead (in the previous step's fused launch), and this step's fused launch
+// runs the next step's.
+cudaError_t launch_step(lbm_ctx *c, cudaStream_t s, bool fused)
 {
-    cudaError_t e = launch_macro(c->kp, 0, c->p.progressive ? 1 : 0, c->sms, s);
+    cudaError_t e = cudaSuccess;
+    if (!fused) e = launch_macro(c->kp, 0, c->p.progressive ? 1 : 0, c->sms, s);
     if (e == cudaSuccess && c->p.progressive) e = launch_activate(c->kp, 0, c->sms, s);
-    if (e == cudaSuccess) e = launch_collide(c->kp, 0, c->sms, s);
+    if (e == cudaSuccess) e = fused ? launch_fused(c->kp, c->sms, s) : launch_collide(c->kp, 0, c->sms, s);
     return e;
 }
 
-// Two steps captured as a graph (once; dropped when the parameters change).
-int ensure_graph(lbm_ctx *c)
+// Whether the steps may run fused.
+bool fusable(const lbm_ctx *c)
 {
+    return c->fuse && c->kp.cflag && (c->exec == LBM_EXEC_STREAM || c->exec == LBM_EXEC_GRAPH);
+}
+
+// Two steps captured as a graph (once; dropped when the parameters change).
+int ensure_graph(lbm_ctx *c, bool fused)
+{
+    if (c->gexec && c->graph_fused != fused) drop_graph(c);
     if (c->gexec) return LBM_OK;
     if (!c->cap) CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     CUDA_OR_FAIL(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_step(c, c->cap);
-    if (e == cudaSuccess) e = launch_step(c, c->cap);
+    cudaError_t e = launch_step(c, c->cap, fused);
+    if (e == cudaSuccess) e = launch_step(c, c->cap, fused);
+    c->graph_fused = fused;
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -412,12 +477,17 @@ bool sort_point(const lbm_ctx *c, int t)
     return c->sort_period > 0 && c->p.progressive && t > 0 && t % c->sort_period == 0;
 }
 
+// A step that ends fused leaves the next step's pass 1 done, its candidates
+// marked; a renumbering must not meet pending candidates, so the step before
+// a renumbering check runs unfused.
+bool fuse_step(const lbm_ctx *c, int t) { return fusable(c) && !sort_point(c, t + 1); }
+
 int enqueue_steps(lbm_ctx *c, int nsteps)
 {
     int k = 0;
     while (k < nsteps) {
         const int t = (int)(c->step + k);
-        if (sort_point(c, t)) {
+        if (sort_point(c, t) && !c->ahead) {
             // the side stream reads the tables: let its last round finish
             if (c->mlp) CUDA_OR_FAIL(c, cudaStreamWaitEvent(c->stream, c->side_done, 0));
             CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return launch_sort(c->kp, c->sms, c->stream); },
@@ -433,29 +503,59 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
         if (c->sort_period > 0 && c->p.progressive)
             chunk = std::min(chunk, c->sort_period - t % c->sort_period);
         if (c->exec == LBM_EXEC_PERSISTENT) {
+            // (its first pass 1 repeats one that ran ahead, with the same
+            // result: the criterion's marks are idempotent)
             CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] {
                              return launch_run(c->kp, chunk, c->p.progressive ? 1 : 0, c->sms, c->stream);
                          }));
+            c->ahead = false;
+            c->fz_clean = false;
             k += chunk;
             continue;
         }
-        if (c->exec == LBM_EXEC_GRAPH && chunk >= 2) {
-            int rc = ensure_graph(c);
-            if (rc) return rc;
-            for (int p = 0; p < chunk / 2; ++p)
-                CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return cudaGraphLaunch(c->gexec, c->stream); },
-                                      2 * (c->p.progressive ? 4 : 2)));
-            k += 2 * (chunk / 2);
-            continue;
+        if (c->exec == LBM_EXEC_GRAPH) {
+            const bool fz = fusable(c);
+            // fused: the last step before a renumbering check runs unfused
+            const int ng = fz && sort_point(c, t + chunk) ? chunk - 1 : chunk;
+            if (ng >= 2) {
+                if (fz && !c->ahead) {
+                    CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
+                                     return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
+                                 }));
+                    c->ahead = true;
+                }
+                int rc = ensure_graph(c, fz);
+                if (rc) return rc;
+                if (fz && !c->fz_clean) {
+                    CUDA_OR_FAIL(c, cudaMemsetAsync(c->kp.cflag, 0, cflag_bytes(c->capacity), c->stream));
+                    c->fz_clean = true;
+                }
+                const int per_step = (fz ? 1 : 2) + (c->p.progressive ? 2 : 0);
+                for (int p = 0; p < ng / 2; ++p)
+                    CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return cudaGraphLaunch(c->gexec, c->stream); },
+                                          2 * per_step));
+                c->ahead = fz;
+                if (!fz) c->fz_clean = false;
+                k += 2 * (ng / 2);
+                continue;
+            }
         }
-        CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
-                         return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
-                     }));
+        if (!c->ahead)
+            CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
+                             return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
+                         }));
         if (c->p.progressive)
             CUDA_OR_FAIL(c, timed(c, K_ACTIVATE,
                                   [&] { return launch_activate(c->kp, t, c->sms, c->stream); },
                                   2));  // k_order + k_activate
-        CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, c->sms, c->stream); }));
+        if (fuse_step(c, t)) {
+            CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return fused_launch(c, c->stream); }));
+            c->ahead = true;
+        } else {
+            CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, c->sms, c->stream); }));
+            c->ahead = false;
+            c->fz_clean = false;
+        }
         k += 1;
     }
     c->step += nsteps;
@@ -558,6 +658,8 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
     const bool aa = p->streaming == LBM_STREAM_AA;
     k.aa = aa ? 1 : 0;
     k.buf_stride = aa ? 0 : one_buf;
+    const bool fz = !dev16 && !aa && p->ncomp == 2;
+    k.strip = auto_strip(c->nbx, c->nby);
     struct Want {
         void **dst;
         size_t bytes;
@@ -580,6 +682,9 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
         {(void **)&k.ctrl, sizeof(Ctrl)},
         {(void **)&c->mass_partial, (size_t)c->capacity * 2 * sizeof(double)},
         {(void **)&c->mass_out, 2 * sizeof(double)},
+        // fused step (FP32, two components, A-B)
+        {(void **)&k.cflag, fz ? cflag_bytes(c->capacity) : 0},
+        {(void **)&k.fz_hist, fz ? (size_t)FZ_BINS * sizeof(int) : 0},
     };
     for (auto &w : want) {
         if (w.bytes == 0) {
@@ -601,6 +706,11 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
     if (!c->stage) {
         fail(c, LBM_ENOMEM, "staging allocation failed");
         return bail(LBM_ENOMEM);
+    }
+    if (fz && (cudaMemsetAsync(k.cflag, 0, cflag_bytes(c->capacity), c->stream) != cudaSuccess ||
+               cudaMemsetAsync(k.fz_hist, 0, (size_t)FZ_BINS * sizeof(int), c->stream) != cudaSuccess)) {
+        fail(c, LBM_ECUDA, "memset failed");
+        return bail(LBM_ECUDA);
     }
     if (cudaMemsetAsync(k.ctrl, 0, sizeof(Ctrl), c->stream) != cudaSuccess) {
         fail(c, LBM_ECUDA, "memset failed");
@@ -684,15 +794,17 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
                 }
             }
     std::vector<int> slot_of(nb, AMBIENT), block_of;
-    long long nonsolid_blocks = 0;
     for (long long b = 0; b < nb; ++b) {
         if (c->nonsolid_h[b] == 0) {
             slot_of[b] = SOLIDBLK;
             for (int w = 0; w < MASK_WORDS; ++w) c->solid_h[b * MASK_WORDS + w] = 0xffffffffu;
-            continue;
         }
-        ++nonsolid_blocks;
-        if (!p.progressive || differs[b]) {
+    }
+    // initial slots in the slot order (block order, or strips of block rows)
+    c->kp.strip = c->strip_rows < 0 ? auto_strip(c->nbx, c->nby) : (c->strip_rows >= c->nby ? 0 : c->strip_rows);
+    for (long long r = 0; r < nb; ++r) {
+        const long long b = strip_block((int)r, c->nbx, c->nby, c->nbz, c->kp.strip);
+        if (c->nonsolid_h[b] > 0 && (!p.progressive || differs[b])) {
             slot_of[b] = (int)block_of.size();
             block_of.push_back((int)b);
         }
@@ -760,6 +872,8 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
         CUDA_OR_FAIL(c, cudaStreamSynchronize(s));
     }
     CUDA_OR_FAIL(c, cudaMemsetAsync(k.cand_mark, 0, nb * sizeof(unsigned), s));
+    c->ahead = false;
+    c->fz_clean = false;
     {
         std::vector<int> act(nb, -1);
         for (int sl = 0; sl < n0; ++sl) act[block_of[sl]] = 0;
@@ -769,6 +883,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     if (c->prep) CUDA_OR_FAIL(c, cudaMemsetAsync(c->prep, 0, nb * sizeof(unsigned), s));
     Ctrl ctrl{};
     ctrl.n_active[0] = ctrl.n_active[1] = n0;
+    ctrl.fz_dist = lag_distance(nbr_rows, n0);
     CUDA_OR_FAIL(c, cudaMemcpyAsync(k.ctrl, &ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice, s));
     if (k.mac_stride)
         CUDA_OR_FAIL(c, cudaMemsetAsync(k.mac, 0, 2 * k.mac_stride * sizeof(float4), s));
@@ -945,10 +1060,13 @@ int lbm_get_block_populations(lbm_ctx *c, int32_t block_id, float *out)
     if (!c->geometry) return fail(c, LBM_ESTATE, "lbm_set_geometry has not been called");
     if (block_id < 0 || block_id >= c->nblocks) return fail(c, LBM_EINVAL, "block %d out of range", block_id);
     DeviceGuard g(c->device);
-    int slot = -1;
+    int slot = -1, na = 0;
+    int rc = active_count(c, &na);
+    if (rc) return rc;
     CUDA_OR_FAIL(c, cudaMemcpyAsync(&slot, c->kp.slot_of + block_id, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CUDA_OR_FAIL(c, cudaStreamSynchronize(c->stream));
-    if (slot < 0) return fail(c, LBM_EINVAL, "block %d is not meshed", block_id);
+    // (a candidate already marked for the next step holds a slot >= na)
+    if (slot < 0 || slot >= na) return fail(c, LBM_EINVAL, "block %d is not meshed", block_id);
     const int rd = (int)(c->step & 1);
     const bool gather = !c->kp.f || c->kp.aa;  // 16-bit forms decode, A-A gathers
     const float *src = !gather ? c->kp.f + (size_t)rd * c->kp.buf_stride + (size_t)slot * c->kp.slot_floats
@@ -1000,6 +1118,9 @@ int lbm_get_stats(lbm_ctx *c, lbm_stats *out)
         out->prepared_blocks = (long long)ctrl.prepared;
         out->prepared_hits = (long long)ctrl.prepared_hits;
         out->slot_sorts = (long long)ctrl.sorts;
+        out->fused_deferred = (long long)ctrl.fz_deferred;
+        out->fused_waited = (long long)ctrl.fz_waited;
+        out->fused_lag_distance = ctrl.fz_dist;
         long long ns = 0;
         for (int v : c->nonsolid_h) ns += v > 0;
         out->nonsolid_blocks = ns;
@@ -1142,6 +1263,27 @@ int lbm_set_slot_order(lbm_ctx *c, int period)
     if (!c) return LBM_EINVAL;
     if (period < 0) return fail(c, LBM_EINVAL, "period must be >= 0");
     c->sort_period = period;
+    return LBM_OK;
+}
+
+int lbm_set_slot_strip(lbm_ctx *c, int rows)
+{
+    if (!c) return LBM_EINVAL;
+    if (rows < -1) return fail(c, LBM_EINVAL, "rows must be >= -1");
+    c->strip_rows = rows;
+    c->kp.strip = rows < 0 ? auto_strip(c->nbx, c->nby) : (rows >= c->nby ? 0 : rows);
+    drop_graph(c);
+    return LBM_OK;
+}
+
+int lbm_set_fusion(lbm_ctx *c, int on, int max_lag)
+{
+    if (!c) return LBM_EINVAL;
+    if (on != 0 && on != 1) return fail(c, LBM_EINVAL, "on must be 0 or 1");
+    if (max_lag < 0) return fail(c, LBM_EINVAL, "max_lag must be >= 0");
+    c->fuse = on != 0;
+    c->kp.fz_max_lag = max_lag;
+    drop_graph(c);
     return LBM_OK;
 }
 

@@ -52,7 +52,23 @@ struct Ctrl {
     unsigned long long sorts;           // renumberings of the slots in block order
     int sort_go;       // the renumbering under way moves the slots
     int n_sorted;      // A-A: the first n_sorted work items visit kp.order
+    // fused step launch (collision of step t + pass 1 of step t + 1)
+    int fz_dist;       // neighbour slot distance that covers most slots (the lag)
+    unsigned fz_hist_ctas;  // CTAs of k_sort_tables done with the distance histogram
+    unsigned long long fz_deferred;  // pass-1 items skipped and redone at the end of their CTA's
+                                     // sequence, summed over launches
+    unsigned long long fz_waited;    // pass-1 warp items that found a collision unfinished
 };
+
+// Neighbour-distance histogram of the fused step's lag: bins of FZ_BIN
+// slots, the last one open-ended.  The lag covers the distance of
+// FZ_COVER_PERMIL / 1000 of the slots; the others are deferred.
+constexpr int FZ_BINS = 1024;
+constexpr int FZ_BIN = 8;
+constexpr int FZ_COVER_PERMIL = 900;
+// Default cap of the lag, in half-block work items: the populations written
+// and read during the lag must stay in the 126 MB of L2.
+constexpr int FZ_MAX_LAG = 1536;
 
 // Everything a kernel needs, passed by value.
 struct KParams {
@@ -119,6 +135,13 @@ struct KParams {
     int *order;             // A-A: [capacity] slots in block order (the first
                             // ctrl->n_sorted of them); the passes visit them
                             // in this order instead of moving the blocks
+    // fused step (FP32, two components, A-B)
+    int *cflag;             // [2][capacity * 2]: per step parity and half block, the
+                            // warps that have finished its collision
+    int *fz_hist;           // [FZ_BINS]: neighbour distances of the slots (renumbering)
+    int fz_max_lag;         // cap of the lag in work items
+    int strip;              // slot order: strips of this many block rows along y
+                            // (each strip in z, y, x order); 0 = block order
 };
 
 // Kernel kinds for per-kernel timing.
@@ -142,6 +165,9 @@ struct StorageOps {
     cudaError_t (*run)(const KParams &, int, int, int, cudaStream_t);
     // between steps: renumber the meshed slots in block order when due
     cudaError_t (*sort)(const KParams &, int, cudaStream_t);
+    // the collision of a step and pass 1 of the next in one launch (FP32,
+    // two components, A-B only; cudaErrorNotSupported otherwise)
+    cudaError_t (*fused)(const KParams &, int, cudaStream_t);
 };
 const StorageOps *storage_ops_fp32();
 const StorageOps *storage_ops_fp32_16x8x4();
@@ -164,6 +190,21 @@ cudaError_t launch_ambient_slot(const KParams &kp, cudaStream_t s);
 cudaError_t launch_macro(const KParams &kp, int step, int criterion, int sms, cudaStream_t s);
 cudaError_t launch_activate(const KParams &kp, int step, int sms, cudaStream_t s);
 cudaError_t launch_collide(const KParams &kp, int step, int sms, cudaStream_t s);
+// The collision of the step and pass 1 (with the criterion in progressive
+// mode) of the next one, in one launch.
+cudaError_t launch_fused(const KParams &kp, int sms, cudaStream_t s);
+// Block-order rank r -> block id in the slot order of kp.strip (host and
+// device share the definition).
+__host__ __device__ inline int strip_block(int r, int nbx, int nby, int nbz, int strip)
+{
+    if (strip <= 0 || strip >= nby) return r;
+    const int full = strip * nbx * nbz;  // blocks of a full strip
+    const int k = r / full;
+    const int h = (k + 1) * strip <= nby ? strip : nby - k * strip;  // rows of strip k
+    const int rr = r - k * full;
+    const int z = rr / (nbx * h), rem = rr % (nbx * h);
+    return rem % nbx + nbx * (k * strip + rem / nbx + nby * z);
+}
 cudaError_t launch_output(const KParams &kp, int rd, int comp, int slot0, int nslots, float *out,
                           int sms, cudaStream_t s);
 cudaError_t launch_mass(const KParams &kp, int rd, int n, double *partial, double *out, int grid,

@@ -134,6 +134,8 @@ cudaError_t launch_collide(const KParams &kp, int step, int sms, cudaStream_t s)
     return ops_of(kp).collide(kp, step, sms, s);
 }
 
+cudaError_t launch_fused(const KParams &kp, int sms, cudaStream_t s) { return ops_of(kp).fused(kp, sms, s); }
+
 cudaError_t launch_output(const KParams &kp, int rd, int comp, int slot0, int nslots, float *out,
                           int sms, cudaStream_t s)
 {

@@ -484,9 +484,21 @@ __device__ __forceinline__ void pull(const KParams &kp, const WarpNbr &wn,
     }
 }
 
+// Load of a population.  CG: through L2 only (ld.global.cg), for values
+// written earlier in the same launch by other CTAs (the fused step); else
+// through the read-only path.
+template <bool CG>
+__device__ __forceinline__ float ldpop(const float *p)
+{
+    if constexpr (CG)
+        return __ldcg(p);
+    else
+        return __ldg(p);
+}
+
 // pull() of the FP32 form for two components, handing both components of
 // each direction to sink(I, (f_0, f_1)) together.
-template <class Sink>
+template <bool CG = false, class Sink>
 __device__ __forceinline__ void pull2_f32(const KParams &kp, const WarpNbr &wn, const float *rd,
                                           int own_slot, int c, int lx, int ly, int lz, uint32_t bits,
                                           bool live, Sink &&sink)
@@ -504,7 +516,7 @@ __device__ __forceinline__ void pull2_f32(const KParams &kp, const WarpNbr &wn, 
     });
     float2 v[Q];
     Unroll<0, Q>::run([&]<int I>() {
-        v[I] = live ? make_float2(__ldg(rd + off[I]), __ldg(rd + off[I] + Q * CELLS))
+        v[I] = live ? make_float2(ldpop<CG>(rd + off[I]), ldpop<CG>(rd + off[I] + Q * CELLS))
                     : make_float2(0.f, 0.f);
     });
     sink.template operator()<0>(v[0]);
@@ -937,8 +949,9 @@ __device__ __forceinline__ void macro_cell(const KParams &kp, const WarpNbr &wn,
 
 // Eq. 13 at a fluid cell bordering unmeshed blocks: when the velocity of a
 // component changed by more than S since the previous step, the unmeshed
-// blocks next to the cell become candidates.  Warp-collective.
-template <int NC>
+// blocks next to the cell become candidates.  Warp-collective.  CG: the
+// previous velocity was written in the same launch (fused step).
+template <int NC, bool CG = false>
 __device__ __forceinline__ void criterion_mark(const KParams &kp, Ctrl *ctrl, int par, int n, int slot,
                                                int c, const WarpNbr &wn, bool fluid,
                                                const float u[2][3])
@@ -951,7 +964,17 @@ __device__ __forceinline__ void criterion_mark(const KParams &kp, Ctrl *ctrl, in
 #pragma unroll
         for (int a = 0; a < NC; ++a) {
             const float *up = kp.uprev + ((size_t)slot * NC + a) * 3 * CELLS + c;
-            const float dx = u[a][0] - up[0], dy = u[a][1] - up[CELLS], dz = u[a][2] - up[2 * CELLS];
+            float p0, p1, p2;
+            if constexpr (CG) {
+                p0 = __ldcg(up);
+                p1 = __ldcg(up + CELLS);
+                p2 = __ldcg(up + 2 * CELLS);
+            } else {
+                p0 = up[0];
+                p1 = up[CELLS];
+                p2 = up[2 * CELLS];
+            }
+            const float dx = u[a][0] - p0, dy = u[a][1] - p1, dz = u[a][2] - p2;
             d2max = fmaxf(d2max, dx * dx + dy * dy + dz * dz);
         }
         if (d2max > kp.S2) tgt = front;
@@ -1241,9 +1264,11 @@ __global__ void __launch_bounds__(1024) k_sort_rank(KParams kp)
     // A-A: no idle buffer to move the blocks through; the passes visit the
     // slots in this order instead
     int *perm = kp.aa ? kp.order : kp.cand_list;
+    // rank r of the slot order (block order, or strips of block rows)
+    auto blk = [&](int r) { return strip_block(r, kp.nbx, kp.nby, kp.nbz, kp.strip); };
     scan_blocks(
-        kp.nbx * kp.nby * kp.nbz, [&](int b) { return kp.slot_of[b] >= 0; },
-        [&](int b, int r) { perm[r] = kp.slot_of[b]; });
+        kp.nbx * kp.nby * kp.nbz, [&](int r) { return kp.slot_of[blk(r)] >= 0; },
+        [&](int r, int k) { perm[k] = kp.slot_of[blk(r)]; });
     if (kp.aa && threadIdx.x == 0) {
         ctrl->n_sorted = n;
         ctrl->sorted_created = ctrl->created;
@@ -1327,9 +1352,13 @@ __global__ void __launch_bounds__(THREADS) k_sort_aux(KParams kp)
 }
 
 // The neighbour-slot table of the renumbered slots (as warp_nbr), and the
-// bookkeeping of the renumbering.
+// bookkeeping of the renumbering.  With the fused step, also the distance
+// from each slot to its farthest meshed neighbour, as a histogram; the last
+// CTA turns it into ctrl->fz_dist, the distance that covers FZ_COVER_PERMIL
+// per mille of the slots (the fused step's lag; the rest are deferred).
 __global__ void __launch_bounds__(THREADS) k_sort_tables(KParams kp)
 {
+    __shared__ int last;
     Ctrl *ctrl = kp.ctrl;
     if (!ctrl->sort_go) return;
     const int n = ctrl->n_active[ctrl->step & 1];
@@ -1343,11 +1372,37 @@ __global__ void __launch_bounds__(THREADS) k_sort_tables(KParams kp)
             if (nid >= 0) v = kp.slot_of[nid];
         }
         kp.nbr[(size_t)s * NBR_STRIDE + lane] = v;
+        if (kp.fz_hist) {
+            const int far = __reduce_max_sync(FULL, v);
+            if (lane == 0) atomicAdd(&kp.fz_hist[min((far - s) / FZ_BIN, FZ_BINS - 1)], 1);
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->sorted_created = ctrl->created;
         ctrl->sorts += 1ull;
     }
+    if (!kp.fz_hist) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&ctrl->fz_hist_ctas, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        const long long need = ((long long)n * FZ_COVER_PERMIL + 999) / 1000;
+        long long cum = 0;
+        int b = 0;
+        for (; b < FZ_BINS - 1; ++b) {
+            cum += __ldcg(kp.fz_hist + b);
+            if (cum >= need) break;
+        }
+        ctrl->fz_dist = (b + 1) * FZ_BIN;
+        ctrl->fz_hist_ctas = 0u;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < FZ_BINS; b += blockDim.x) kp.fz_hist[b] = 0;
 }
 
 // A-A: one cell of a block created in this step.  Its incoming
@@ -1788,8 +1843,64 @@ __device__ __forceinline__ float2 edot(const float2 *a, const float2 *na)
     return r;
 }
 
-// Pass 1 of a step, FP32 form with two components, paired arithmetic (as
-// k_macro).
+// One work item of pass 1, FP32 form with two components, paired
+// arithmetic (as k_macro): streaming and moments of the cells c of one half
+// block (row: the slot's neighbour-table entry of this lane, bits: the
+// cell's solid word); with `criterion`, Eq. 13 at cells bordering unmeshed
+// blocks.  par, n: the step's parity and meshed count.  CG: the populations
+// and previous velocities were written earlier in the same launch.  All
+// lanes of the warp call.
+// Called by the item functions once the pull's loads are consumed (the
+// fused step publishes the previous item's completion there).
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+template <bool CG, class Hook = NoHook>
+__device__ __forceinline__ void macro2_item(const KParams &kp, Ctrl *ctrl, const float *rd, int par, int n,
+                                            int slot, int c, int row, uint32_t bits, int criterion,
+                                            Hook &&hook = Hook{})
+{
+    const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
+    const WarpNbr wn = warp_nbr_of(kp, row);
+    const bool live = !(bits & 1u);
+    const bool held = (bits >> HELD_BIT) & 1u;
+    if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) {
+        hook();
+        return;
+    }
+    if (!criterion || wn.amb == 0u) {
+        // warp-uniform: no cell of the warp borders an unmeshed block, so
+        // the criterion has nothing to test and only the densities are
+        // needed (summed in the same order as Moments2)
+        float2 rho = make_float2(0.f, 0.f);
+        pull2_f32<CG>(kp, wn, rd, slot, c, lx, ly, lz, bits, live,
+                      [&]<int I>(float2 v) { rho = add2(rho, v); });
+        hook();
+        kp.mac[(size_t)slot * CELLS + c] =
+            live ? mac_pack(rho.x, psi_of(kp, rho.x), rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    Moments2 m;
+    pull2_f32<CG>(kp, wn, rd, slot, c, lx, ly, lz, bits, live,
+                  [&]<int I>(float2 v) { m.template add<I>(v); });
+    hook();
+    const float2 inv = make_float2(1.f / m.rho.x, 1.f / m.rho.y);
+    float u[2][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float2 ud = mul2(m.j[d], inv);
+        u[0][d] = ud.x;
+        u[1][d] = ud.y;
+    }
+    // solid cells write zeros too (never read): complete sectors
+    kp.mac[(size_t)slot * CELLS + c] =
+        live ? mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+    criterion_mark<2, CG>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
+}
+
+// Pass 1 of a step, FP32 form with two components (grid-stride over the
+// half-block items of the meshed slots).
 __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int criterion)
 {
     Ctrl *ctrl = kp.ctrl;
@@ -1806,43 +1917,14 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
-        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const int row = next_row;
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
         if (it2 < total) {
             next_row = nbr_row_lane(kp, it2 / PARTS);
             next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
-        const bool live = !(bits & 1u);
-        const bool held = (bits >> HELD_BIT) & 1u;
-        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
-        if (!criterion || wn.amb == 0u) {
-            // warp-uniform: no cell of the warp borders an unmeshed block, so
-            // the criterion has nothing to test and only the densities are
-            // needed (summed in the same order as Moments2)
-            float2 rho = make_float2(0.f, 0.f);
-            pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live,
-                      [&]<int I>(float2 v) { rho = add2(rho, v); });
-            kp.mac[(size_t)slot * CELLS + c] =
-                live ? mac_pack(rho.x, psi_of(kp, rho.x), rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
-            continue;
-        }
-        Moments2 m;
-        pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live,
-                  [&]<int I>(float2 v) { m.template add<I>(v); });
-        const float2 inv = make_float2(1.f / m.rho.x, 1.f / m.rho.y);
-        float u[2][3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const float2 ud = mul2(m.j[d], inv);
-            u[0][d] = ud.x;
-            u[1][d] = ud.y;
-        }
-        // solid cells write zeros too (never read): complete sectors
-        kp.mac[(size_t)slot * CELLS + c] =
-            live ? mac_pack(m.rho.x, psi_of(kp, m.rho.x), m.rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
-        criterion_mark<2>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
+        macro2_item<false>(kp, ctrl, rd, par, n, slot, c, row, bits, criterion);
     }
 }
 
@@ -1851,8 +1933,88 @@ __global__ void __launch_bounds__(THREADS, 3) k_macro2(KParams kp, int criterion
     macro2_body(kp, kp.ctrl->step, criterion);
 }
 
-// Pass 2 of a step, FP32 form with two components, paired arithmetic (as
-// k_collide).
+// One work item of pass 2, FP32 form with two components, paired
+// arithmetic (as k_collide): streaming again, forces from the neighbours'
+// mac, forced BGK collision into the write buffer, the velocity kept at
+// cells bordering unmeshed blocks.  All lanes of the warp call.
+template <bool TAU1, class Hook = NoHook>
+__device__ __forceinline__ void collide2_item(const KParams &kp, const float *rd, float *wr, int slot, int c,
+                                              int row, uint32_t bits, Hook &&hook = Hook{})
+{
+    const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
+    const WarpNbr wn = warp_nbr_of(kp, row);
+    const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+    // every lane takes part in the ballot (it must not sit behind &&)
+    const bool row_live = row_has(live);
+    const bool fill = (bits & 1u) && row_live;  // solid cell completing a sector
+    if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) {
+        hook();
+        return;
+    }
+    Moments2 m;
+    float2 fin[TAU1 ? 1 : Q];
+    pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live, [&]<int I>(float2 v) {
+        m.template add<I>(v);
+        if constexpr (!TAU1) fin[I] = v;
+    });
+    hook();
+    const float2 rho = m.rho;
+    const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
+    float2 u[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
+    float2 F[3];
+    forces2<2>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
+    if (!live && !fill) return;
+    float2 v[3], nv[3], nu[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        v[d] = fma2(F[d], inv, u[d]);
+        nv[d] = sub2(make_float2(0.f, 0.f), v[d]);
+        nu[d] = sub2(make_float2(0.f, 0.f), u[d]);
+    }
+    const float2 one = splat(1.f);
+    const float2 cv = fma2(splat(-1.5f), fma2(v[0], v[0], fma2(v[1], v[1], mul2(v[2], v[2]))), one);
+    const float2 cu = fma2(splat(-1.5f), fma2(u[0], u[0], fma2(u[1], u[1], mul2(u[2], u[2]))), one);
+    float2 wrho[3];
+    Unroll<0, 3>::run([&]<int K>() {
+        constexpr int I = K == 0 ? 0 : (K == 1 ? 1 : 5);
+        wrho[K] = mul2(splat(wgt(I)), rho);
+    });
+    const float2 relax = splat(1.f - kp.omega);
+    float2 moving = make_float2(0.f, 0.f);
+    float *d0 = wr + (size_t)slot * kp.slot_floats + c;
+    float *d1 = d0 + Q * CELLS;
+    // the 18 moving populations (Eqs. 10-12); the rest population from
+    // the mass balance sum_i f_i = rho (see k_collide)
+    Unroll<1, Q>::run([&]<int I>() {
+        const float2 ev = edot<I>(v, nv);
+        float2 f = mul2(wrho[wclass(I)], fma2(ev, fma2(ev, splat(4.5f), splat(3.f)), cv));
+        if constexpr (!TAU1) {
+            const float2 eu = edot<I>(u, nu);
+            const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
+            f = fma2(relax, sub2(fin[I], e0), f);
+        }
+        moving = add2(moving, f);
+        d0[I * CELLS] = live ? f.x : 0.f;
+        d1[I * CELLS] = live ? f.y : 0.f;
+    });
+    const float2 rest = sub2(rho, moving);
+    d0[0] = live ? rest.x : 0.f;
+    d1[0] = live ? rest.y : 0.f;
+    (void)cu;
+    if (live && kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
+        float *up = kp.uprev + (size_t)slot * 2 * 3 * CELLS + c;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            up[d * CELLS] = u[d].x;
+            up[(3 + d) * CELLS] = u[d].y;
+        }
+    }
+}
+
+// Pass 2 of a step, FP32 form with two components (grid-stride over the
+// half-block items).
 template <bool TAU1>
 __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
 {
@@ -1875,78 +2037,14 @@ __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
-        const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
-        const WarpNbr wn = warp_nbr_of(kp, next_row);
+        const int row = next_row;
         const uint32_t bits = next_bits;
         const int it2 = it + gridDim.x;
         if (it2 < total) {
             next_row = nbr_row_lane(kp, it2 / PARTS);
             next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
-        const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
-        // every lane takes part in the ballot (it must not sit behind &&)
-        const bool row_live = row_has(live);
-        const bool fill = (bits & 1u) && row_live;  // solid cell completing a sector
-        if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) continue;
-        Moments2 m;
-        float2 fin[TAU1 ? 1 : Q];
-        pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live, [&]<int I>(float2 v) {
-            m.template add<I>(v);
-            if constexpr (!TAU1) fin[I] = v;
-        });
-        const float2 rho = m.rho;
-        const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
-        float2 u[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
-        float2 F[3];
-        forces2<2>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
-        if (!live && !fill) continue;
-        float2 v[3], nv[3], nu[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            v[d] = fma2(F[d], inv, u[d]);
-            nv[d] = sub2(make_float2(0.f, 0.f), v[d]);
-            nu[d] = sub2(make_float2(0.f, 0.f), u[d]);
-        }
-        const float2 one = splat(1.f);
-        const float2 cv = fma2(splat(-1.5f), fma2(v[0], v[0], fma2(v[1], v[1], mul2(v[2], v[2]))), one);
-        const float2 cu = fma2(splat(-1.5f), fma2(u[0], u[0], fma2(u[1], u[1], mul2(u[2], u[2]))), one);
-        float2 wrho[3];
-        Unroll<0, 3>::run([&]<int K>() {
-            constexpr int I = K == 0 ? 0 : (K == 1 ? 1 : 5);
-            wrho[K] = mul2(splat(wgt(I)), rho);
-        });
-        const float2 relax = splat(1.f - kp.omega);
-        float2 moving = make_float2(0.f, 0.f);
-        float *d0 = wr + (size_t)slot * kp.slot_floats + c;
-        float *d1 = d0 + Q * CELLS;
-        // the 18 moving populations (Eqs. 10-12); the rest population from
-        // the mass balance sum_i f_i = rho (see k_collide)
-        Unroll<1, Q>::run([&]<int I>() {
-            const float2 ev = edot<I>(v, nv);
-            float2 f = mul2(wrho[wclass(I)], fma2(ev, fma2(ev, splat(4.5f), splat(3.f)), cv));
-            if constexpr (!TAU1) {
-                const float2 eu = edot<I>(u, nu);
-                const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
-                f = fma2(relax, sub2(fin[I], e0), f);
-            }
-            moving = add2(moving, f);
-            d0[I * CELLS] = live ? f.x : 0.f;
-            d1[I * CELLS] = live ? f.y : 0.f;
-        });
-        const float2 rest = sub2(rho, moving);
-        d0[0] = live ? rest.x : 0.f;
-        d1[0] = live ? rest.y : 0.f;
-        (void)cu;
-        if (live && kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
-            float *up = kp.uprev + (size_t)slot * 2 * 3 * CELLS + c;
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                up[d * CELLS] = u[d].x;
-                up[(3 + d) * CELLS] = u[d].y;
-            }
-        }
+        collide2_item<TAU1>(kp, rd, wr, slot, c, row, bits);
     }
 }
 
@@ -1956,6 +2054,238 @@ __global__ void __launch_bounds__(THREADS, 2) k_collide2(KParams kp)
     const int step = *(volatile const int *)&kp.ctrl->step;
     collide2_body<TAU1>(kp, step);
     step_done(kp.ctrl, step);
+}
+
+// ---- fused step: the collision of step t and pass 1 of step t + 1 -----------
+// (FP32, two components, A-B.)  One launch runs both passes over the meshed
+// slots, so that pass 1 reads the populations the collision has just written
+// while they are still in L2, instead of from HBM in a launch of its own:
+// every population crosses HBM once per step in each direction.
+//
+// Pass 1 of a half block reads the new populations of its block and of its
+// 26 neighbours, and rewrites its block's mac, which the neighbours'
+// collisions read.  So it starts only once the collisions of all 27 blocks
+// have finished: every warp of a collision item adds 1 to the item's
+// counter (release) after its own stores, and pass 1 waits until the
+// counters of its neighbourhood read WARPS_PER_ITEM (acquire), then reads
+// the populations and previous velocities through L2 (ld.global.cg).  The
+// counters come in two parities by step: a launch counts in one and clears
+// the other for the next launch (the host clears both after an unfused step).
+//
+// The work is a fixed sequence: the first L collision items, then collision
+// and pass-1 items alternately, then the remaining pass-1 items; CTA g takes
+// positions g, g + G, ... in order, its warps each their own rows of every
+// item, with no CTA barrier.  The lag L is about the slot distance of a
+// block's farthest neighbour (ctrl->fz_dist, see k_sort_tables) plus one
+// round of the grid, so that the collisions a pass-1 item needs are a round
+// or more behind it.  A pass-1 item waits only for collisions placed before
+// it; one whose neighbourhood holds a collision placed after it (a block
+// meshed since the last renumbering, a neighbour across a periodic boundary
+// or a strip border) is skipped and redone once the CTA's sequence is
+// through.  Waits thus only ever point back in the sequence, and every
+// wait is bounded anyway (LBM_ETIMEOUT).  The results equal those of
+// k_collide2 + k_macro2 bit for bit: the same item code computes every value.
+
+// A strong (L2) load without acquire semantics: polling with acquire loads
+// would invalidate the SM's L1 at every poll, under the other warps'
+// cached data.  The polled counters are released by their writers; the data
+// they guard is then read through L2 (ld.global.cg), so no stale L1 line
+// can be seen.
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+// Positions in the work sequence of C collision and C pass-1 items with lag
+// L (0 <= L <= C), and the item at a position q < 2C.
+__device__ __forceinline__ int fz_pos_collide(int i, int L) { return i < L ? i : 2 * i - L; }
+enum FzKind { FZ_COLLIDE = 0, FZ_PASS1 = 1 };
+__device__ __forceinline__ int fz_item(int q, int C, int L, int &idx)
+{
+    if (q < L) {
+        idx = q;
+        return FZ_COLLIDE;
+    }
+    if (q < 2 * C - L) {
+        const int r = (q - L) >> 1;
+        idx = ((q - L) & 1) ? r : L + r;
+        return ((q - L) & 1) ? FZ_PASS1 : FZ_COLLIDE;
+    }
+    idx = q - C;
+    return FZ_PASS1;
+}
+
+constexpr int WARPS_PER_ITEM = THREADS / 32;
+
+// Whether pass-1 item j at position q of the sequence has a collision of its
+// neighbourhood (the largest slot `far` of its table row) placed after it.
+__device__ __forceinline__ bool fz_far(int far, int q, int L)
+{
+    return fz_pos_collide(PARTS * far + PARTS - 1, L) > q;
+}
+
+template <bool TAU1>
+__global__ void __launch_bounds__(THREADS, 2) k_fused2(KParams kp)
+{
+    Ctrl *ctrl = kp.ctrl;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int step = *(volatile const int *)&ctrl->step;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par ^ 1];
+    const bool run = *(volatile int *)&ctrl->status == 0 && in_range(kp, n, (long long)kp.capacity + 1, 7);
+    const int C = run ? n * PARTS : 0;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;  // read by the collision
+    float *wr = kp.f + (size_t)(par ^ 1) * kp.buf_stride;   // its output, read by pass 1
+    // arrival counters of this launch, and the other parity's (cleared for
+    // the next launch)
+    int *cnt = kp.cflag + (size_t)par * kp.capacity * PARTS;
+    int *cnt_next = kp.cflag + (size_t)(par ^ 1) * kp.capacity * PARTS;
+    const int G = gridDim.x;
+    int L = PARTS * (*(volatile int *)&ctrl->fz_dist + 1) + G;
+    L = min(L, kp.fz_max_lag > 0 ? kp.fz_max_lag : FZ_MAX_LAG);
+    L = max(0, min(L, C));
+    if (run && blockIdx.x == 0 && tid == 0) {
+        ctrl->cell_updates += (unsigned long long)n * CELLS;
+        ctrl->fluid_updates += ctrl->fluid_active;
+    }
+    unsigned long long waited = 0, deferred = 0;  // lane 0 of warp 0: statistics
+    // This warp's part of the last collision item, not yet counted: it is
+    // counted once the next item's loads are consumed, when its stores have
+    // long reached L2 and the fence before the count costs little.
+    int pending = -1;
+    auto publish = [&]() {
+        if (pending >= 0) {
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicAdd(cnt + pending, 1);
+            }
+            pending = -1;
+        }
+    };
+
+    // Pass 1 of item idx after its neighbourhood's collisions (all lanes of
+    // the warp call).  `ready`: the counters were already seen complete.
+    auto pass1 = [&](int idx, int row, uint32_t bits, bool ready, auto &&hook) {
+        publish();  // never wait while holding an uncounted collision part
+        bool ok = true, w = false;
+        if (!__all_sync(FULL, ready) && row >= 0) {
+#pragma unroll
+            for (int p = 0; p < PARTS; ++p) {
+                const int *fl = cnt + PARTS * row + p;
+                for (long long it = 0; ld_relaxed(fl) < WARPS_PER_ITEM; ++it) {
+                    w = true;
+                    // give up after the poll limit, or once the launch has
+                    if (it > kp.barrier_spins ||
+                        ((it & 255) == 255 && *(volatile int *)&ctrl->status != 0)) {
+                        ok = false;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                if (!ok) break;
+            }
+        }
+        __syncwarp();  // the lanes' observations order every lane's loads below
+        ok = __all_sync(FULL, ok);
+        if (__any_sync(FULL, w) && tid == 0) ++waited;
+        if (!ok) {
+            if (lane == 0) atomicCAS(&ctrl->status, 0, LBM_ETIMEOUT);
+            return;
+        }
+        macro2_item<true>(kp, ctrl, wr, par ^ 1, n, idx / PARTS, (idx % PARTS) * THREADS + tid, row, bits,
+                          kp.progressive, hook);
+    };
+
+    const int total = 2 * C;
+    int q = blockIdx.x;
+    int idx0;
+    int next_row = SOLIDBLK;
+    uint32_t next_bits = 1u;
+    if (q < total) {
+        fz_item(q, C, L, idx0);
+        next_row = nbr_row_lane(kp, idx0 / PARTS);
+        next_bits = kp.nbits[(size_t)(idx0 / PARTS) * CELLS + (idx0 % PARTS) * THREADS + tid];
+    }
+    // counters of the next pass-1 item's neighbourhood, read half an item
+    // ahead (once its table row is in): complete counters stay complete
+    bool next_ready = false;
+    for (; q < total; q += G) {
+        int idx;
+        const int kind = fz_item(q, C, L, idx);
+        const int row = next_row;
+        const uint32_t bits = next_bits;
+        const bool ready = next_ready;
+        next_ready = false;
+        int i2 = 0, kind2 = -1;
+        if (q + G < total) {
+            kind2 = fz_item(q + G, C, L, i2);
+            next_row = nbr_row_lane(kp, i2 / PARTS);
+            next_bits = kp.nbits[(size_t)(i2 / PARTS) * CELLS + (i2 % PARTS) * THREADS + tid];
+        }
+        // after the current item's loads: count the last collision part,
+        // look at the next pass-1 item's counters
+        auto hook = [&]() {
+            publish();
+            if (kind2 == FZ_PASS1) {
+                bool r = true;
+                if (next_row >= 0) {
+#pragma unroll
+                    for (int p = 0; p < PARTS; ++p) r = r && ld_relaxed(cnt + PARTS * next_row + p) >= WARPS_PER_ITEM;
+                }
+                next_ready = r;
+            }
+        };
+        // (warp-uniform: lane 0's reading) the launch gave up
+        if (__shfl_sync(FULL, *(volatile int *)&ctrl->status, 0) != 0) continue;
+        if (kind == FZ_COLLIDE) {
+            if (tid == 0) cnt_next[idx] = 0;
+            collide2_item<TAU1>(kp, rd, wr, idx / PARTS, (idx % PARTS) * THREADS + tid, row, bits, hook);
+            pending = idx;
+        } else if (fz_far(__reduce_max_sync(FULL, row), q, L)) {
+            if (tid == 0) ++deferred;  // redone below (lane 13 of row holds the slot itself)
+        } else {
+            pass1(idx, row, bits, ready, hook);
+        }
+    }
+    publish();
+    // the skipped pass-1 items of this CTA, every collision now placed before them
+    for (q = blockIdx.x; q < total; q += G) {
+        int idx;
+        if (fz_item(q, C, L, idx) != FZ_PASS1) continue;
+        const int row = nbr_row_lane(kp, idx / PARTS);
+        if (!fz_far(__reduce_max_sync(FULL, row), q, L)) continue;
+        if (__shfl_sync(FULL, *(volatile int *)&ctrl->status, 0) != 0) break;
+        pass1(idx, row, kp.nbits[(size_t)(idx / PARTS) * CELLS + (idx % PARTS) * THREADS + tid], false,
+              NoHook{});
+    }
+    if (tid == 0) {
+        if (waited) atomicAdd(&ctrl->fz_waited, waited);
+        if (deferred) atomicAdd(&ctrl->fz_deferred, deferred);
+    }
+    // the last CTA advances the step
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&ctrl->collide_done, 1u) == gridDim.x - 1) {
+            ctrl->collide_done = 0u;
+            if (ctrl->status == 0) ctrl->step = step + 1;
+            __threadfence();
+        }
+    }
 }
 
 // ---- A-A streaming: the two passes (FP32, two components) -------------------
@@ -2776,7 +3106,10 @@ __global__ void __launch_bounds__(THREADS) k_features(KParams kp, int par, const
                 }
             } else if (warp == 6 && lane < 27 && lane != 13) {
                 const int nid = neighbour_of(kp, gid, lane);
-                out[8 + lane - (lane > 13 ? 1 : 0)] = (nid >= 0 && kp.slot_of[nid] >= 0) ? 1.f : 0.f;
+                // (a candidate of the next step, already marked, has a slot
+                // at or beyond nmesh: not meshed yet)
+                const int ns = nid >= 0 ? kp.slot_of[nid] : SOLIDBLK;
+                out[8 + lane - (lane > 13 ? 1 : 0)] = (ns >= 0 && ns < nmesh) ? 1.f : 0.f;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -2899,6 +3232,20 @@ template <auto Kern, class... A>
 cudaError_t launch_persistent(int sms, cudaStream_t s, A... args)
 {
     Kern<<<sms * occupancy<Kern>(), THREADS, 0, s>>>(args...);
+    return cudaGetLastError();
+}
+
+// Launch of the fused step: the resident CTAs less one when their number is
+// even.  CTA g takes positions g, g + G, ... of a sequence that alternates
+// collision and pass-1 items by position, so an odd G makes every CTA
+// alternate too (an even G would give half the CTAs only collisions and the
+// other half only pass-1 items, which then wait on them).
+template <auto Kern, class... A>
+cudaError_t launch_fused_grid(int sms, cudaStream_t s, A... args)
+{
+    int g = sms * occupancy<Kern>();
+    if (g > 1 && (g & 1) == 0) g -= 1;
+    Kern<<<g, THREADS, 0, s>>>(args...);
     return cudaGetLastError();
 }
 
@@ -3072,11 +3419,21 @@ struct Launch {
         k_sort_tables<<<sms * 2, THREADS, 0, s>>>(kp);
         return cudaGetLastError();
     }
+    static cudaError_t fused(const KParams &kp, int sms, cudaStream_t s)
+    {
+        if constexpr (Store<ST>::DEV) {
+            return cudaErrorNotSupported;
+        } else {
+            if (kp.ncomp != 2 || kp.aa || !kp.cflag) return cudaErrorNotSupported;
+            if (kp.omega == 1.0f) return launch_fused_grid<k_fused2<true>>(sms, s, kp);
+            return launch_fused_grid<k_fused2<false>>(sms, s, kp);
+        }
+    }
     static const StorageOps *ops()
     {
         static const StorageOps table = {init,    init_finish,  ambient_slot, macro,    activate,    collide,
                                          output,  mass_partial, block_pops,   features, ctas_per_sm, run,
-                                         sort};
+                                         sort,    fused};
         return &table;
     }
 };

@@ -61,6 +61,8 @@ class Stats(C.Structure):
         ("kernel_ms", C.c_double * 4), ("kernel_launches", C.c_longlong * 4),
         ("created_blocks", C.c_longlong), ("prepared_blocks", C.c_longlong),
         ("prepared_hits", C.c_longlong), ("slot_sorts", C.c_longlong),
+        ("fused_deferred", C.c_longlong), ("fused_waited", C.c_longlong),
+        ("fused_lag_distance", C.c_longlong),
     ]
 
 
@@ -70,7 +72,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_step", "lbm_ste
            "lbm_last_error", "lbm_mass_noalloc", "lbm_frontier_features", "lbm_activation_steps",
            "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_set_params", "lbm_mlp_get_params",
            "lbm_mlp_set_scaling", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
-           "lbm_set_proposer", "lbm_set_exec", "lbm_barrier_selftest", "lbm_set_slot_order"]
+           "lbm_set_proposer", "lbm_set_exec", "lbm_barrier_selftest", "lbm_set_slot_order",
+           "lbm_set_slot_strip", "lbm_set_fusion"]
 NOALLOC_MAX_BLOCKS = 65536
 MLP_IN, MLP_HIDDEN = 34, 64
 MLP_NPARAM = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
@@ -124,6 +127,8 @@ def load():
     lib.lbm_set_exec.argtypes = [vp, C.c_int]
     lib.lbm_barrier_selftest.argtypes = [C.c_int, C.c_longlong]
     lib.lbm_set_slot_order.argtypes = [vp, C.c_int]
+    lib.lbm_set_slot_strip.argtypes = [vp, C.c_int]
+    lib.lbm_set_fusion.argtypes = [vp, C.c_int, C.c_int]
     for name in EXPORTS:
         if name != "lbm_last_error":
             getattr(lib, name).restype = C.c_int
@@ -193,7 +198,9 @@ class LBM:
     grav, rho_ref, S, max_blocks.  ``stream``: a
     torch.cuda.Stream (default: the current stream).  ``torch_alloc``:
     allocate through torch's caching allocator (default) or let the library
-    use cudaMallocAsync.
+    use cudaMallocAsync.  ``slot_strip`` (lbm_set_slot_strip, before the
+    geometry) and ``fusion`` = (on, max_lag) (lbm_set_fusion) are applied
+    right after the context is created when given.
     """
 
     def __init__(self, stream=None, torch_alloc=True, **kw):
@@ -242,6 +249,8 @@ class LBM:
         p.rho_ref[1] = float(rr[1]) if len(rr) > 1 else 0.0
         p.S = float(kw.get("S", 0.0))
         p.max_blocks = int(kw.get("max_blocks", 0))
+        strip = kw.get("slot_strip", None)
+        fusion = kw.get("fusion", None)
         self._alloc = None
         if torch_alloc:
             self._alloc = _TorchAllocator(torch, self.device, self.torch_stream.cuda_stream)
@@ -254,6 +263,10 @@ class LBM:
         if rc != OK:
             raise LBMError(rc, self.lib.lbm_last_error(None).decode())
         self.h = h
+        if strip is not None:
+            self.set_slot_strip(strip)
+        if fusion is not None:
+            self.set_fusion(*fusion)
 
     # -- lifetime
     def close(self):
@@ -377,6 +390,21 @@ def _lbm_set_slot_order(self, period: int):
 
 
 LBM.set_slot_order = _lbm_set_slot_order
+
+
+def _lbm_set_slot_strip(self, rows: int):
+    """Slot order: strips of `rows` block rows (0 block order, -1 automatic;
+    lbm_set_slot_strip; applies at the next set_geometry and renumbering)."""
+    self._check(self.lib.lbm_set_slot_strip(self.h, int(rows)))
+
+
+def _lbm_set_fusion(self, on: bool = True, max_lag: int = 0):
+    """Collision of a step and pass 1 of the next in one launch (lbm_set_fusion)."""
+    self._check(self.lib.lbm_set_fusion(self.h, 1 if on else 0, int(max_lag)))
+
+
+LBM.set_slot_strip = _lbm_set_slot_strip
+LBM.set_fusion = _lbm_set_fusion
 LBM.frontier_features = _lbm_frontier_features
 LBM.activation_steps = _lbm_activation_steps
 LBM.set_proposer = _lbm_set_proposer

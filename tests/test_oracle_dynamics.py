@@ -110,7 +110,6 @@ def test_poiseuille(H, steps):
     assert err * H * H < 0.4
 
 
-@pytest.mark.slow
 def test_laplace_law():
     """Single-component droplets: the pressure jump between the bulk phases
     (EOS at the measured bulk densities) is linear in 1/R with a near-zero
