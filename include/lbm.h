@@ -268,13 +268,20 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  *   mass     host array of ncomp doubles, written on success
  *   stream   cudaStream_t to run on (NULL = default stream); the call waits
  *            for it before returning
- * The sum runs in the same fixed order as lbm_mass.  Every call shares the
- * one scratch array of its device and rewrites every value it reads, so no
- * state carries from one call to the next; calls that overlap on the same
- * GPU (other streams or host threads) race on it and must be serialised by
- * the caller.  The first call on a device looks up the array's device
- * address with that device current (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Errors: LBM_EINVAL, LBM_ECUDA (message in
+ * Each block's partial sum is formed as in lbm_mass (per cell over the 19
+ * populations in order, then over the block's cells), and the partials are
+ * added in row order.  So the result equals lbm_mass bit for bit when the
+ * rows are every block of the grid in block order (none unmeshed, none fully
+ * solid); otherwise it agrees to rounding.  Unlike lbm_mass it adds nothing
+ * for blocks that are not passed (lbm_mass counts unmeshed blocks at the
+ * ambient state).  Every call shares the one scratch array of its device and
+ * rewrites every value it reads, so no state carries from one call to the
+ * next; calls that overlap on the same GPU (other streams or host threads)
+ * race on it and must be serialised by the caller.  Each call looks up the
+ * array's device address on the current device (cudaGetSymbolAddress), so
+ * the address stays valid after a cudaDeviceReset; the first call on a
+ * device also loads the library's device code there, so make that first call
+ * before any stream capture.  Errors: LBM_EINVAL, LBM_ECUDA (message in
  * lbm_last_error(NULL)). */
 int lbm_mass_noalloc(const float *f, const uint32_t *solid, long long nblocks, int ncomp,
                      double *mass, void *stream);

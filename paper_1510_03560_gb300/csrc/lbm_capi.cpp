@@ -530,7 +530,7 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
                     CUDA_OR_FAIL(c, cudaMemsetAsync(c->kp.cflag, 0, cflag_bytes(c->capacity), c->stream));
                     c->fz_clean = true;
                 }
-                const int per_step = (fz ? 1 : 2) + (c->p.progressive ? 2 : 0);
+                const int per_step = (fz ? 1 : 2) + (c->p.progressive ? 1 : 0);
                 for (int p = 0; p < ng / 2; ++p)
                     CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return cudaGraphLaunch(c->gexec, c->stream); },
                                           2 * per_step));
@@ -546,8 +546,7 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
                          }));
         if (c->p.progressive)
             CUDA_OR_FAIL(c, timed(c, K_ACTIVATE,
-                                  [&] { return launch_activate(c->kp, t, c->sms, c->stream); },
-                                  2));  // k_order + k_activate
+                                  [&] { return launch_activate(c->kp, t, c->sms, c->stream); }));
         if (fuse_step(c, t)) {
             CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return fused_launch(c, c->stream); }));
             c->ahead = true;

@@ -50,6 +50,7 @@ struct Ctrl {
     long long check_value;  // and the offending value
     unsigned long long sorted_created;  // `created` at the last renumbering of the slots
     unsigned long long sorts;           // renumberings of the slots in block order
+    unsigned macro_done;  // CTAs of the current pass-1 launch that finished
     int sort_go;       // the renumbering under way moves the slots
     int n_sorted;      // A-A: the first n_sorted work items visit kp.order
     // fused step launch (collision of step t + pass 1 of step t + 1)

@@ -5,7 +5,6 @@
 // caller's allocator.
 #include <cstdint>
 #include <cstdio>
-#include <mutex>
 
 #include "lbm.h"
 #include "lbm_internal.h"
@@ -20,10 +19,6 @@ namespace {
 // cudaGetSymbolAddress below.
 constexpr long long kPartials = (long long)LBM_NOALLOC_MAX_BLOCKS * 2;
 static __device__ __align__(256) double g_noalloc_scratch[kPartials + 2];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_lock;
-double *g_scratch_addr[kMaxDevices] = {};
 
 // Errors are reported through lbm_last_error(NULL).
 int fail(int code, const char *what, cudaError_t e)
@@ -93,22 +88,16 @@ __global__ void __launch_bounds__(1024) k_noalloc_total(const double *partial, i
     if (t < 2) total[t] = red[0][t];
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// Device address of the scratch array on the current device, looked up at
+// every call with that device current: after a cudaDeviceReset the library's
+// module is loaded again and the array may move, so no address is kept from
+// one call to the next.
 int scratch_for_current_device(double **out)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaGetDevice", e);
-    if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EINVAL, "device index out of range", cudaSuccess);
-    std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaGetSymbolAddress", e);
-        g_scratch_addr[dev] = (double *)p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaGetSymbolAddress", e);
+    *out = (double *)p;
     return LBM_OK;
 }
 
@@ -129,11 +118,13 @@ extern "C" int lbm_mass_noalloc(const float *f, const uint32_t *solid, long long
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     int sms = 1, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaGetDevice", e);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return fail(LBM_ECUDA, "cudaDeviceGetAttribute", e);
     const int grid = (int)(nblocks < 4LL * sms ? nblocks : 4LL * sms);
     k_noalloc_partial<<<grid, CELLS, 0, s>>>(f, solid, (int)nblocks, ncomp, scratch);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return fail(LBM_ECUDA, "partial-sum launch", e);
     k_noalloc_total<<<1, 1024, 0, s>>>(scratch, (int)nblocks, scratch + kPartials);
     e = cudaGetLastError();

@@ -35,12 +35,14 @@
 //
 // One time step is these launches:
 //   k_macro    pull streaming + Eqs. 4-5 + Eqs. 6-7 -> mac; criterion of
-//              Eq. 13 at cells bordering unmeshed blocks, marking targets
-//   k_order    the step's candidates renumbered in block order
+//              Eq. 13 at cells bordering unmeshed blocks, marking targets;
+//              its last CTA renumbers the step's candidates in block order
 //   k_activate new blocks: slots, ambient equilibrium, their k_macro work
 //   k_collide  pull streaming again + forces (Eqs. 8-9, gravity,
 //              adhesion) from the neighbours' mac + forced BGK collision
 //              (Eqs. 10-12) -> f of the other buffer
+// (or, fused, k_fused2: the collision of a step and k_macro's work for the
+// next one in a single launch, see below)
 // Between steps, now and then, the k_sort_* launches renumber the meshed
 // slots in block order (locality; "slot order" below).  Further sections:
 // A-A streaming (one population array, Sec. 3), the TMA-staged and
@@ -91,6 +93,10 @@ __device__ __forceinline__ void step_done(Ctrl *ctrl, int step)
         }
     }
 }
+
+// The candidates of a step renumbered in block order by the last CTA of the
+// launch that marked them (defined with order_body below).
+__device__ void order_tail(const KParams &kp, int step);
 
 constexpr int THREADS = 256;            // threads per CTA of the cell kernels
 // resident CTAs per SM the deviation-form step kernels are compiled for
@@ -1027,8 +1033,17 @@ __device__ __forceinline__ void macro_body(const KParams &kp, int step, int crit
         const bool held = (bits >> HELD_BIT) & 1u;
         // (warp-uniform: the pull below shuffles)
         if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
-        float rho[2], u[2][3];
         const float ref[2] = {0.f, 0.f};
+        if (!criterion || wn.amb == 0u) {
+            // warp-uniform: nothing for the criterion to test, only the
+            // densities are needed (summed in the order of Moments)
+            float r[2] = {0.f, 0.f};
+            pull<NC, ST>(kp, wn, rd, slot, c, lx, ly, lz, bits, live, false, ref,
+                         [&]<int I>(int a, float v) { r[a] += v; });
+            if (live) kp.mac[(size_t)slot * CELLS + c] = mac_pack(r[0], psi_of(kp, r[0]), NC == 2 ? r[1] : 0.f);
+            continue;
+        }
+        float rho[2], u[2][3];
         macro_cell<NC, ST>(kp, wn, rd, kp.mac, slot, c, lx, ly, lz, bits, live, false, ref,
                            make_float4(0.f, 0.f, 0.f, 0.f), rho, u);
         if (criterion) criterion_mark<NC>(kp, ctrl, par, n, slot, c, wn, live && !held, u);
@@ -1038,7 +1053,9 @@ __device__ __forceinline__ void macro_body(const KParams &kp, int step, int crit
 template <int NC>
 __global__ void __launch_bounds__(THREADS) k_macro(KParams kp, int criterion)
 {
-    macro_body<NC>(kp, kp.ctrl->step, criterion);
+    const int step = kp.ctrl->step;
+    macro_body<NC>(kp, step, criterion);
+    if (criterion) order_tail(kp, step);
 }
 
 // Per weight class: w rho_prev (the references of a cell's incoming values)
@@ -1122,6 +1139,19 @@ __device__ __forceinline__ void macro_dev_body(const KParams &kp, int step, int 
             const bool held = (cur.bits >> HELD_BIT) & 1u;
             float2 wref[3], famb[3];
             amb_and_refs(kp, cur.ref, wref, famb);
+            if (!criterion || cur.wn.amb == 0u) {
+                // warp-uniform: nothing for the criterion to test, only the
+                // densities are needed (summed in the order of Moments2)
+                float2 rho = make_float2(0.f, 0.f);
+                dev_consume2<ST>(cur.L, wref, famb, [&]<int I>(float2 v) { rho = add2(rho, v); });
+                if (live)
+                    mac[(size_t)cur.slot * CELLS + cur.c] =
+                        held ? mac_pack(cur.ref.x, psi_of(kp, cur.ref.x), cur.ref.y)
+                             : mac_pack(rho.x, psi_of(kp, rho.x), NC == 2 ? rho.y : 0.f);
+                cur = nxt;
+                it2 += G;
+                continue;
+            }
             Moments2 m;
             dev_consume2<ST>(cur.L, wref, famb, [&]<int I>(float2 v) { m.template add<I>(v); });
             const float2 inv = make_float2(1.f / m.rho.x, 1.f / m.rho.y);
@@ -1146,7 +1176,9 @@ __device__ __forceinline__ void macro_dev_body(const KParams &kp, int step, int 
 template <int NC, int ST>
 __global__ void __launch_bounds__(THREADS, DEV_MACRO_MIN_CTAS) k_macro_dev(KParams kp, int criterion)
 {
-    macro_dev_body<NC, ST>(kp, kp.ctrl->step, criterion);
+    const int step = kp.ctrl->step;
+    macro_dev_body<NC, ST>(kp, step, criterion);
+    if (criterion) order_tail(kp, step);
 }
 
 // Ranks in ascending block order of the blocks b < nb with pick(b), by a
@@ -1218,9 +1250,9 @@ __device__ __forceinline__ void order_body(const KParams &kp, int step)
 {
     Ctrl *ctrl = kp.ctrl;
     const int par = step & 1;
-    const int n_old = ctrl->n_active[par];
-    const int ncand = ctrl->ncand[par];
-    if (ctrl->status || ncand <= 0 || n_old + ncand > kp.capacity) return;
+    const int n_old = __ldcg(&ctrl->n_active[par]);
+    const int ncand = __ldcg(&ctrl->ncand[par]);
+    if (__ldcg(&ctrl->status) || ncand <= 0 || n_old + ncand > kp.capacity) return;
     scan_blocks(
         kp.nbx * kp.nby * kp.nbz, [&](int b) { return kp.cand_mark[b] == 1u; },
         [&](int b, int r) {
@@ -1229,7 +1261,52 @@ __device__ __forceinline__ void order_body(const KParams &kp, int step)
         });
 }
 
-__global__ void __launch_bounds__(1024) k_order(KParams kp) { order_body(kp, kp.ctrl->step); }
+// The same renumbering by counting, for the usual few candidates of a step:
+// a candidate's rank is the number of candidates with a smaller block id
+// (O(ncand^2 / threads), no pass over every block's mark); bursts of more
+// than ORDER_BY_COUNT candidates take order_body's scan.  The counts were
+// changed by other CTAs' atomics: read through L2.  Every thread of the CTA
+// must call.
+constexpr int ORDER_BY_COUNT = 1024;
+__device__ __forceinline__ void order_candidates(const KParams &kp, int step)
+{
+    __shared__ int cand[ORDER_BY_COUNT];
+    Ctrl *ctrl = kp.ctrl;
+    const int par = step & 1;
+    const int n_old = __ldcg(&ctrl->n_active[par]);
+    const int ncand = __ldcg(&ctrl->ncand[par]);
+    if (__ldcg(&ctrl->status) || ncand <= 0 || n_old + ncand > kp.capacity) return;
+    if (ncand > ORDER_BY_COUNT) {
+        order_body(kp, step);
+        return;
+    }
+    for (int k = threadIdx.x; k < ncand; k += blockDim.x) cand[k] = __ldcg(kp.cand_list + k);
+    __syncthreads();
+    for (int k = threadIdx.x; k < ncand; k += blockDim.x) {
+        const int b = cand[k];
+        int r = 0;
+        for (int j = 0; j < ncand; ++j) r += cand[j] < b;
+        kp.cand_list[r] = b;
+        kp.slot_of[b] = n_old + r;
+    }
+}
+
+// The last CTA of a pass-1 launch renumbers the step's candidates (block
+// creation then needs no launch of its own for it).  Every thread calls.
+__device__ void order_tail(const KParams &kp, int step)
+{
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&kp.ctrl->macro_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) kp.ctrl->macro_done = 0u;
+    order_candidates(kp, step);
+}
 
 // ---- slot order ---------------------------------------------------------------
 // Blocks created by the criterion take the next free slots, so the slot
@@ -1930,7 +2007,9 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
 
 __global__ void __launch_bounds__(THREADS, 3) k_macro2(KParams kp, int criterion)
 {
-    macro2_body(kp, kp.ctrl->step, criterion);
+    const int step = kp.ctrl->step;
+    macro2_body(kp, step, criterion);
+    if (criterion) order_tail(kp, step);
 }
 
 // One work item of pass 2, FP32 form with two components, paired
@@ -2276,15 +2355,22 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused2(KParams kp)
         if (waited) atomicAdd(&ctrl->fz_waited, waited);
         if (deferred) atomicAdd(&ctrl->fz_deferred, deferred);
     }
-    // the last CTA advances the step
+    // the last CTA renumbers the next step's candidates and advances the step
+    __shared__ int last;
     __syncthreads();
     if (tid == 0) {
         __threadfence();
-        if (atomicAdd(&ctrl->collide_done, 1u) == gridDim.x - 1) {
-            ctrl->collide_done = 0u;
-            if (ctrl->status == 0) ctrl->step = step + 1;
-            __threadfence();
-        }
+        last = atomicAdd(&ctrl->collide_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (kp.progressive) order_candidates(kp, step + 1);
+    __syncthreads();
+    if (tid == 0) {
+        ctrl->collide_done = 0u;
+        if (__ldcg(&ctrl->status) == 0) ctrl->step = step + 1;
+        __threadfence();
     }
 }
 
@@ -2324,6 +2410,16 @@ __device__ __forceinline__ void macro_aa_body(const KParams &kp, int step, int c
         const bool live = !(bits & 1u);
         const bool held = (bits >> HELD_BIT) & 1u;
         if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) continue;
+        if (!criterion || wn.amb == 0u) {
+            // warp-uniform: nothing for the criterion to test, only the
+            // densities are needed (summed in the order of Moments2)
+            float2 rho = make_float2(0.f, 0.f);
+            pull2_aa<LOCAL>(kp, wn, slot, c, lx, ly, lz, bits, live, 0u,
+                            [&]<int I>(float2 v) { rho = add2(rho, v); });
+            kp.mac[(size_t)slot * CELLS + c] =
+                live ? mac_pack(rho.x, psi_of(kp, rho.x), rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         Moments2 m;
         pull2_aa<LOCAL>(kp, wn, slot, c, lx, ly, lz, bits, live, 0u,
                         [&]<int I>(float2 v) { m.template add<I>(v); });
@@ -2348,6 +2444,7 @@ __global__ void __launch_bounds__(THREADS, 4) k_macro_aa(KParams kp, int criteri
         macro_aa_body<true>(kp, step, criterion);
     else
         macro_aa_body<false>(kp, step, criterion);
+    if (criterion) order_tail(kp, step);
 }
 
 // The collision writes every non-solid cell: fluid cells their new
@@ -2636,7 +2733,9 @@ __device__ __forceinline__ void macro2_staged_body(const KParams &kp, int step, 
 
 __global__ void __launch_bounds__(TMA_THREADS, 1) k_macro2_staged(KParams kp, int criterion)
 {
-    macro2_staged_body(kp, kp.ctrl->step, criterion);
+    const int step = kp.ctrl->step;
+    macro2_staged_body(kp, step, criterion);
+    if (criterion) order_tail(kp, step);
 }
 
 template <bool TAU1>
@@ -2835,16 +2934,19 @@ __device__ __forceinline__ void collide_dev_body(const KParams &kp, int step)
                     const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
                     f = fma2(relax, sub2(fin[I], e0), f);
                 }
-                moving = add2(moving, f);
                 // the reader's density: the neighbour's, or the cell's own
                 const int tx = lx + cx(I), ty = ly + cy(I), tz = lz + cz(I);
                 const uint32_t mb = __shfl_sync(FULL, cur.wn.mbase, nbk(tx, ty, tz));
                 const bool solid_n = (bits >> opp(I)) & 1u;  // x + e_I = x - e_opp(I)
                 const float2 rr = (solid_n || !nonsolid) ? rho : __ldg(mac2 + 2 * (mb + lcell(tx, ty, tz)));
                 const float2 d = fma2(splat(-wgt(I)), rr, f);
-                if (nonsolid) dst[I * CELLS] = S::enc2(d.x, d.y);
+                const uint32_t h = S::enc2(d.x, d.y);
+                if (nonsolid) dst[I * CELLS] = h;
+                // the value its reader will decode, rounding included
+                moving = add2(moving, add2(S::dec2(h), mul2(splat(wgt(I)), rr)));
             });
-            // rest population from the mass balance sum_i f_i = rho
+            // rest population from the mass balance sum_i f_i = rho over the
+            // stored values: the cell's 16-bit rounding leaves its mass unchanged
             const float2 d0 = fma2(splat(-wgt(0)), rho, sub2(rho, moving));
             if (nonsolid) dst[0] = S::enc2(d0.x, d0.y);
             (void)cu;
@@ -3306,8 +3408,7 @@ struct Launch {
     }
     static cudaError_t activate(const KParams &kp, int step, int sms, cudaStream_t s)
     {
-        k_order<<<1, 1024, 0, s>>>(kp);
-        if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
+        // (the candidates were renumbered in block order by the pass-1 launch)
         if (kp.ncomp == 2)
             k_activate<2, ST><<<sms, THREADS, 0, s>>>(kp);
         else

@@ -238,3 +238,47 @@ def test_proposer_results_are_bit_identical(L, storage):
     prop.close()
     base.close()
     m.close()
+
+
+def test_trained_proposer_gain(L):
+    """What the trained network buys: the 256^3 injection recipe at 128^3
+    with a sphere seed it was not trained on, through the growth of the
+    mesh, with and without the proposer (period 16, threshold 0.5).  The
+    results are bit-identical; the test reports the block-creation time with
+    and without, the share of created blocks that had been prepared, and the
+    bound on any gain, 1 / (1 - creation share of the step time): the
+    proposer can only take work out of block creation."""
+    from paper_1510_03560_gb300 import proposer as PR
+    case = PR.trace_case(1510035620, 128)
+    runs = {}
+    for name in ("without", "with"):
+        sim = L.from_case(case)
+        mlp = PR.load_model(L) if name == "with" else None
+        if mlp is not None:
+            sim.set_proposer(mlp, period=16, threshold=0.5)
+        sim.set_profiling(True)
+        sim.step(400)
+        st = sim.stats()
+        runs[name] = dict(stats=st, act=sim.active_blocks(), rho=[sim.macro(a)[0] for a in range(2)],
+                          mass=sim.mass())
+        sim.set_proposer(None)
+        sim.close()
+        if mlp is not None:
+            mlp.close()
+    a, b = runs["without"], runs["with"]
+    np.testing.assert_array_equal(a["act"], b["act"])
+    for x, y in zip(a["rho"], b["rho"]):
+        np.testing.assert_array_equal(x, y)
+    np.testing.assert_array_equal(a["mass"], b["mass"])
+    sa, sb = a["stats"], b["stats"]
+    share = sa["kernel_ms"][1] / sum(sa["kernel_ms"])
+    bound = 1.0 / (1.0 - share)
+    hit = sb["prepared_hits"] / max(sb["created_blocks"], 1)
+    precision = sb["prepared_hits"] / max(sb["prepared_blocks"], 1)
+    print(f"trained proposer, 128^3, 400 steps: created {sb['created_blocks']}, prepared "
+          f"{sb['prepared_blocks']}, hits {sb['prepared_hits']} ({hit:.0%} of created, {precision:.0%} of "
+          f"prepared); creation {sa['kernel_ms'][1]:.2f} ms without, {sb['kernel_ms'][1]:.2f} ms with; "
+          f"creation share {share:.1%}, so no proposer of this kind can exceed {bound:.3f}x")
+    assert sb["created_blocks"] == sa["created_blocks"] > 0
+    assert sb["prepared_hits"] > 0
+    assert hit > 0.2 and precision > 0.3

@@ -56,6 +56,10 @@ def test_noalloc_mass_matches_lbm_mass(L, which):
     np.testing.assert_allclose(first, want, rtol=1e-6)
     np.testing.assert_allclose(second, want, rtol=1e-6)
     np.testing.assert_array_equal(first, second)
+    if len(ids) == sim.nblocks:
+        # every block of the grid, in block order: the same sums in the same
+        # order as lbm_mass, bit for bit
+        np.testing.assert_array_equal(first, want)
     sim.close()
 
 
