@@ -5,8 +5,14 @@ for the arithmetic, so these runs are not expected to match the oracle to
 the FP32 tolerances.  Each test states the error per field and bounds it:
 
   FP16 (11-bit significand): density <= 1e-3 relative, velocity <= 5e-4.
-  BF16 (8-bit significand, 8x the FP16 rounding step): density <= 1e-2
-  relative, velocity <= 5e-3.
+  BF16 (8-bit significand, 8x the FP16 rounding step): density <= 1e-3
+  relative (the bound the 16-bit forms are specified to) and velocity
+  <= 2e-3, except in the first three fluid layers behind the held inlet of
+  the porous crop (FRONT): there the injected liquid (rho 6.6, accelerated
+  to |v| ~ 0.3 by the forces) meets gas of density 0.34, so the populations
+  a gas cell receives are several times its own density whatever reference
+  they are stored against, and 8 significant bits of them leave up to
+  2e-3 of its density.
 
 With the progressive mesh the 16-bit rounding of the velocity (about 1e-4
 near the injected liquid) is close to the criterion threshold S = 3e-4 of
@@ -28,7 +34,8 @@ from paper_1510_03560_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 BOUNDS = {"fp16": dict(rho=1e-3, u=5e-4, mass=1e-5),
-          "bf16": dict(rho=1e-2, u=5e-3, mass=1e-4)}
+          "bf16": dict(rho=1e-3, u=2e-3, mass=1e-4)}
+FRONT = dict(rho=2e-3, u=2e-3)  # BF16, the first three layers behind the inlet
 TIMING = dict(rho=5e-2, u=2e-2)
 
 
@@ -42,10 +49,12 @@ def L():
     return lbm
 
 
-def field_errors(gpu, orc, case):
+def field_errors(gpu, orc, case, region=None):
     """Max relative density error and max absolute velocity error per
-    component over the non-solid cells."""
+    component over the non-solid cells (of `region` when given)."""
     fluid = case["cell_type"] != 1
+    if region is not None:
+        fluid = fluid & region
     out = []
     for a in range(orc.ncomp):
         g, o = gpu.macro(a), orc.macro(a)
@@ -115,8 +124,17 @@ def test_porous_crop_error_per_field(L, form, progressive):
                 first_diff = (t, len(np.setxor1d(ga, oa)))
     print(f"porous {form} progressive={progressive}: first active-set difference "
           f"(step, blocks) = {first_diff}")
-    check(form, field_errors(gpu, orc, case), f"porous 64^3 crop p={progressive}, 150 steps",
-          TIMING if progressive else None)
+    label = f"porous 64^3 crop p={progressive}, 150 steps"
+    timing = TIMING if first_diff is not None else None
+    if form == "bf16":
+        # the gas cells just behind the inlet (x < 4) take the liquid front
+        # at the 20-fold density contrast: bounded by FRONT, the rest by 1e-3
+        x = np.arange(case["cell_type"].shape[2])[None, None, :]
+        away = np.broadcast_to(x >= 4, case["cell_type"].shape)
+        check(form, field_errors(gpu, orc, case, ~away), label + ", x < 4", timing or FRONT)
+        check(form, field_errors(gpu, orc, case, away), label + ", x >= 4", timing)
+    else:
+        check(form, field_errors(gpu, orc, case), label, timing)
     # held cells keep their state exactly: density from mac, velocity from
     # the stored initial velocity
     held = case["cell_type"] == 2
