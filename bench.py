@@ -183,13 +183,13 @@ def sample_steps(total, warmup, k):
 
 
 def run_timed(L, torch, case, sample, total, progressive, flush, uuid, storage="fp32", proposer=None,
-              exec_mode="stream", streaming="ab", slot_order=64):
+              exec_mode="stream", streaming="ab", slot_order=64, partials=True):
     """Run the whole trajectory of `total` steps, timing the steps listed in
     `sample` one by one (L2 flushed before each, a synchronize on both
     sides); the device time of the whole trajectory is recorded too.
     proposer: an lbm MLP to run the activation proposer with (period 16,
     threshold 0.5).  streaming: "ab" or "aa" (one population array)."""
-    sim = L.from_case(case, progressive=progressive, storage=storage, streaming=streaming)
+    sim = L.from_case(case, progressive=progressive, storage=storage, streaming=streaming, partials=partials)
     sim.set_exec(exec_mode)
     sim.set_slot_order(slot_order)
     if proposer is not None:

@@ -336,6 +336,29 @@ int lbm_set_slot_strip(lbm_ctx *ctx, int rows);
  * Errors: LBM_EINVAL (on not 0 or 1, max_lag < 0). */
 int lbm_set_fusion(lbm_ctx *ctx, int on, int max_lag);
 
+/* Density partials (FP32 storage, two components, A-B streaming; every
+ * execution mode but LBM_EXEC_STAGED; off by default, unused while the fused
+ * step is on: on one GB300 pass 1 moves 6.5x fewer HBM bytes and takes 40 %
+ * less time, but the collision's shared-memory sums and barriers make it 50 %
+ * slower, and the step about 20 % slower).  Pull streaming (Eq. 10, left-hand side) makes a cell's
+ * density at step t + 1 the sum of the post-collision values of step t
+ * that stream into it (Eq. 4), so the collision already holds every term.
+ * Each half block of the collision sums, in shared memory, the terms its
+ * cells pull from the half block itself (one value pair per cell) and the
+ * terms it sends to each cell just outside its faces and edges (stored with
+ * the receiving half block).  Pass 1 of step t + 1 then adds those few
+ * values per cell for the densities and psi (Eqs. 4, 6, 7) instead of
+ * pulling 38 populations; warps next to an unmeshed block still pull, since
+ * the criterion (Eq. 13) needs their velocity.  The sums run in a fixed
+ * order, so every mode and block order gives the same bits; against the
+ * pull they differ only by the rounding of a reordered sum of 19 terms.
+ * Meshed sets and fields still follow the FP64 oracle within the FP32
+ * tolerances.  The first pass 1 after lbm_set_geometry, after switching
+ * them on, or after a collision that did not write them pulls.
+ *   on  1 partials, 0 pull in every pass 1
+ * Errors: LBM_EINVAL (on not 0 or 1). */
+int lbm_set_density_partials(lbm_ctx *ctx, int on);
+
 /* Test hook of the bounded device wait: one cooperative launch whose grid
  * barrier expects `missing` more CTAs than it has, polling at most `spins`
  * times; returns the resulting status (LBM_OK when missing is 0,

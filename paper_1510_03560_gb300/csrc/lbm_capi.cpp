@@ -105,6 +105,11 @@ struct lbm_ctx {
     bool ahead = false;  // pass 1 (with the criterion) of the next step has run
     bool fz_clean = false;  // the arrival counters are set for the next fused launch
     int strip_rows = -1; // slot order: -1 automatic, 0 block order, > 0 strip rows
+    // density partials (FP32, two components, A-B; off by default): the
+    // collision writes them, the next pass 1 sums them instead of pulling
+    bool partials = false;
+    bool part_ok = false;     // the last collision wrote them for the current state
+    bool graph_part = false;  // the step graph was captured with them
 };
 
 namespace {
@@ -429,34 +434,63 @@ void drop_graph(lbm_ctx *c)
     c->graph = nullptr;
 }
 
-// The launches of one step on stream s.  Fused: the step's pass 1 has run
-// ahead (in the previous step's fused launch), and this step's fused launch
-// runs the next step's.
-cudaError_t launch_step(lbm_ctx *c, cudaStream_t s, bool fused)
-{
-    cudaError_t e = cudaSuccess;
-    if (!fused) e = launch_macro(c->kp, 0, c->p.progressive ? 1 : 0, c->sms, s);
-    if (e == cudaSuccess && c->p.progressive) e = launch_activate(c->kp, 0, c->sms, s);
-    if (e == cudaSuccess) e = fused ? launch_fused(c->kp, c->sms, s) : launch_collide(c->kp, 0, c->sms, s);
-    return e;
-}
-
 // Whether the steps may run fused.
 bool fusable(const lbm_ctx *c)
 {
     return c->fuse && c->kp.cflag && (c->exec == LBM_EXEC_STREAM || c->exec == LBM_EXEC_GRAPH);
 }
 
+// Whether the collisions write the density partials and pass 1 sums them
+// (not with the TMA-staged kernels or the fused step, which keep the pull).
+bool part_mode(const lbm_ctx *c) { return c->partials && c->kp.part && !c->kp.staged && !fusable(c); }
+
+// Pass 1 of step t on stream s (criterion in progressive mode), from the
+// partials when the last collision wrote them (then two launches with a
+// progressive mesh: the warps that border unmeshed blocks pull in the
+// second).
+cudaError_t macro_on(lbm_ctx *c, int t, cudaStream_t s)
+{
+    c->kp.part_in = part_mode(c) && c->part_ok ? 1 : 0;
+    return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, s);
+}
+int macro_launches(const lbm_ctx *c, bool part_in) { return part_in && c->p.progressive ? 2 : 1; }
+
+cudaError_t collide_on(lbm_ctx *c, int t, cudaStream_t s)
+{
+    c->kp.part_out = part_mode(c) ? 1 : 0;
+    c->part_ok = part_mode(c);
+    return launch_collide(c->kp, t, c->sms, s);
+}
+
+// The launches of one step on stream s.  Fused: the step's pass 1 has run
+// ahead (in the previous step's fused launch), and this step's fused launch
+// runs the next step's.
+// With the density partials every pass 1 of the graph sums them: it is
+// replayed only after a collision wrote them.
+cudaError_t launch_step(lbm_ctx *c, cudaStream_t s, bool fused)
+{
+    cudaError_t e = cudaSuccess;
+    if (!fused) {
+        c->kp.part_in = part_mode(c) ? 1 : 0;
+        e = launch_macro(c->kp, 0, c->p.progressive ? 1 : 0, c->sms, s);
+    }
+    if (e == cudaSuccess && c->p.progressive) e = launch_activate(c->kp, 0, c->sms, s);
+    c->kp.part_out = part_mode(c) ? 1 : 0;
+    if (e == cudaSuccess) e = fused ? launch_fused(c->kp, c->sms, s) : launch_collide(c->kp, 0, c->sms, s);
+    return e;
+}
+
 // Two steps captured as a graph (once; dropped when the parameters change).
 int ensure_graph(lbm_ctx *c, bool fused)
 {
-    if (c->gexec && c->graph_fused != fused) drop_graph(c);
+    if (c->gexec && (c->graph_fused != fused || c->graph_part != part_mode(c))) drop_graph(c);
     if (c->gexec) return LBM_OK;
     if (!c->cap) CUDA_OR_FAIL(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     CUDA_OR_FAIL(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = launch_step(c, c->cap, fused);
     if (e == cudaSuccess) e = launch_step(c, c->cap, fused);
     c->graph_fused = fused;
+    c->graph_part = part_mode(c);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -505,6 +539,9 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
         if (c->exec == LBM_EXEC_PERSISTENT) {
             // (its first pass 1 repeats one that ran ahead, with the same
             // result: the criterion's marks are idempotent)
+            c->kp.part_in = part_mode(c) && c->part_ok ? 1 : 0;
+            c->kp.part_out = part_mode(c) ? 1 : 0;
+            c->part_ok = part_mode(c);
             CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] {
                              return launch_run(c->kp, chunk, c->p.progressive ? 1 : 0, c->sms, c->stream);
                          }));
@@ -517,11 +554,11 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
             const bool fz = fusable(c);
             // fused: the last step before a renumbering check runs unfused
             const int ng = fz && sort_point(c, t + chunk) ? chunk - 1 : chunk;
-            if (ng >= 2) {
+            // (the graph's passes 1 sum the density partials: a plain step
+            // writes them first)
+            if (ng >= 2 && (!part_mode(c) || c->part_ok)) {
                 if (fz && !c->ahead) {
-                    CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
-                                     return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
-                                 }));
+                    CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] { return macro_on(c, t, c->stream); }));
                     c->ahead = true;
                 }
                 int rc = ensure_graph(c, fz);
@@ -530,28 +567,30 @@ int enqueue_steps(lbm_ctx *c, int nsteps)
                     CUDA_OR_FAIL(c, cudaMemsetAsync(c->kp.cflag, 0, cflag_bytes(c->capacity), c->stream));
                     c->fz_clean = true;
                 }
-                const int per_step = (fz ? 1 : 2) + (c->p.progressive ? 1 : 0);
+                const int per_step =
+                    (fz ? 1 : 1 + macro_launches(c, part_mode(c))) + (c->p.progressive ? 1 : 0);
                 for (int p = 0; p < ng / 2; ++p)
                     CUDA_OR_FAIL(c, timed(c, K_OTHER, [&] { return cudaGraphLaunch(c->gexec, c->stream); },
                                           2 * per_step));
                 c->ahead = fz;
                 if (!fz) c->fz_clean = false;
+                c->part_ok = part_mode(c);
                 k += 2 * (ng / 2);
                 continue;
             }
         }
         if (!c->ahead)
-            CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] {
-                             return launch_macro(c->kp, t, c->p.progressive ? 1 : 0, c->sms, c->stream);
-                         }));
+            CUDA_OR_FAIL(c, timed(c, K_MACRO, [&] { return macro_on(c, t, c->stream); },
+                                  macro_launches(c, part_mode(c) && c->part_ok)));
         if (c->p.progressive)
             CUDA_OR_FAIL(c, timed(c, K_ACTIVATE,
                                   [&] { return launch_activate(c->kp, t, c->sms, c->stream); }));
         if (fuse_step(c, t)) {
             CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return fused_launch(c, c->stream); }));
             c->ahead = true;
+            c->part_ok = false;
         } else {
-            CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return launch_collide(c->kp, t, c->sms, c->stream); }));
+            CUDA_OR_FAIL(c, timed(c, K_COLLIDE, [&] { return collide_on(c, t, c->stream); }));
             c->ahead = false;
             c->fz_clean = false;
         }
@@ -684,6 +723,9 @@ int lbm_create(const lbm_params *p, lbm_ctx **out)
         // fused step (FP32, two components, A-B)
         {(void **)&k.cflag, fz ? cflag_bytes(c->capacity) : 0},
         {(void **)&k.fz_hist, fz ? (size_t)FZ_BINS * sizeof(int) : 0},
+        // density partials (likewise)
+        {(void **)&k.part, fz ? (size_t)c->capacity * CELLS * sizeof(float2) : 0},
+        {(void **)&k.recv, fz ? (size_t)c->capacity * 2 * recv_entries(sh.x, sh.y, sh.z) * sizeof(float2) : 0},
     };
     for (auto &w : want) {
         if (w.bytes == 0) {
@@ -873,6 +915,7 @@ int lbm_set_geometry(lbm_ctx *c, const uint8_t *cell_type, const float *rho_init
     CUDA_OR_FAIL(c, cudaMemsetAsync(k.cand_mark, 0, nb * sizeof(unsigned), s));
     c->ahead = false;
     c->fz_clean = false;
+    c->part_ok = false;
     {
         std::vector<int> act(nb, -1);
         for (int sl = 0; sl < n0; ++sl) act[block_of[sl]] = 0;
@@ -979,8 +1022,9 @@ int lbm_get_macro(lbm_ctx *c, int comp, float *rho, float *ux, float *uy, float 
     std::vector<int> block_of(n);
     CUDA_OR_FAIL(c, cudaMemcpyAsync(block_of.data(), c->kp.block_of, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     const int rd = (int)(c->step & 1);
+    c->kp.part_in = part_mode(c) && c->part_ok ? 1 : 0;
     CUDA_OR_FAIL(c, launch_macro(c->kp, (int)c->step, 0, c->sms, c->stream));
-    c->launches += 1;
+    c->launches += macro_launches(c, c->kp.part_in != 0);
     const int per_chunk = (int)(c->stage_floats / (4 * CELLS));
     std::vector<float> host((size_t)per_chunk * 4 * CELLS);
     for (int s0 = 0; s0 < n; s0 += per_chunk) {
@@ -1282,6 +1326,17 @@ int lbm_set_fusion(lbm_ctx *c, int on, int max_lag)
     if (max_lag < 0) return fail(c, LBM_EINVAL, "max_lag must be >= 0");
     c->fuse = on != 0;
     c->kp.fz_max_lag = max_lag;
+    drop_graph(c);
+    return LBM_OK;
+}
+
+int lbm_set_density_partials(lbm_ctx *c, int on)
+{
+    if (!c) return LBM_EINVAL;
+    if (on != 0 && on != 1) return fail(c, LBM_EINVAL, "on must be 0 or 1");
+    c->partials = on != 0;
+    // the next pass 1 pulls; the partials are written again by the next collision
+    c->part_ok = false;
     drop_graph(c);
     return LBM_OK;
 }

@@ -143,7 +143,23 @@ struct KParams {
     int fz_max_lag;         // cap of the lag in work items
     int strip;              // slot order: strips of this many block rows along y
                             // (each strip in z, y, x order); 0 = block order
+    // density partials (FP32, two components, A-B): written by the collision
+    // of a step, summed by pass 1 of the next one instead of its pull
+    float2 *part;           // [capacity][CELLS]: per cell, the sum of the values it
+                            // will pull from its own half block
+    float2 *recv;           // [capacity][2][recv_entries]: per half block, what its
+                            // neighbour half blocks send to its boundary cells
+    int part_in;            // pass 1 sums the partials (where no neighbour block is unmeshed)
+    int part_out;           // the collision writes them
 };
+
+// Entries of the density partials of one half block (blocks split in two
+// along z): one per cell just outside one of its 6 faces or 12 edges (the
+// corners are out of reach of D3Q19).
+__host__ __device__ constexpr int recv_entries(int bx, int by, int bz)
+{
+    return 2 * (by * (bz / 2) + bx * (bz / 2) + bx * by) + 4 * (bx + by + bz / 2);
+}
 
 // Kernel kinds for per-kernel timing.
 enum KernelKind { K_MACRO = 0, K_ACTIVATE = 1, K_COLLIDE = 2, K_OTHER = 3 };

@@ -504,10 +504,15 @@ __device__ __forceinline__ float ldpop(const float *p)
 
 // pull() of the FP32 form for two components, handing both components of
 // each direction to sink(I, (f_0, f_1)) together.
-template <bool CG = false, class Sink>
+// mid() runs between issuing the loads and the first sink (work that can
+// overlap their latency).
+struct NoMid {
+    __device__ __forceinline__ void operator()() const {}
+};
+template <bool CG = false, class Sink, class Mid = NoMid>
 __device__ __forceinline__ void pull2_f32(const KParams &kp, const WarpNbr &wn, const float *rd,
                                           int own_slot, int c, int lx, int ly, int lz, uint32_t bits,
-                                          bool live, Sink &&sink)
+                                          bool live, Sink &&sink, Mid &&mid = Mid{})
 {
     const uint32_t own = (uint32_t)own_slot * (uint32_t)kp.slot_floats + (uint32_t)c;
     const bool held = (bits >> HELD_BIT) & 1u;
@@ -525,6 +530,7 @@ __device__ __forceinline__ void pull2_f32(const KParams &kp, const WarpNbr &wn, 
         v[I] = live ? make_float2(ldpop<CG>(rd + off[I]), ldpop<CG>(rd + off[I] + Q * CELLS))
                     : make_float2(0.f, 0.f);
     });
+    mid();
     sink.template operator()<0>(v[0]);
     Unroll<0, NPAIR>::run([&]<int P>() {
         sink.template operator()<pair_rep(P)>(v[pair_rep(P)]);
@@ -1318,7 +1324,8 @@ __device__ void order_tail(const KParams &kp, int step)
 // 1/16 of the meshed ones: k_sort_rank decides and ranks the blocks
 // (perm[new slot] = old slot, in cand_list, free between steps), k_sort_aux
 // moves the solid words, the previous velocities, the 16-bit forms'
-// previous densities and block_of through the other population buffer
+// previous densities, the density partials and block_of through the other
+// population buffer
 // (idle between steps), k_sort_move / k_sort_back then move the populations
 // of the next step's read buffer through it, which leaves both buffers
 // holding them, and k_sort_tables
@@ -1390,8 +1397,10 @@ __global__ void __launch_bounds__(THREADS) k_sort_back(KParams kp)
 }
 
 // The per-slot words of the other arrays (solid words, previous velocities,
-// 16-bit forms' previous densities as a float4 per cell, block_of) into slot
-// `new` of the other population buffer, packed, or back (BACK).
+// 16-bit forms' previous densities as a float4 per cell, density partials,
+// block_of) into slot `new` of the other population buffer, packed, or back
+// (BACK).  (A partial entry belongs to the half block that receives it, so
+// it moves with that slot.)
 template <int ST, bool BACK>
 __global__ void __launch_bounds__(THREADS) k_sort_aux(KParams kp)
 {
@@ -1404,7 +1413,11 @@ __global__ void __launch_bounds__(THREADS) k_sort_aux(KParams kp)
     uint32_t *macp = reinterpret_cast<uint32_t *>(kp.mac + (size_t)(par ^ 1) * kp.mac_stride);
     const int nup = kp.uprev ? kp.ncomp * 3 * CELLS : 0;
     const int nmac = Store<ST>::DEV ? 4 * CELLS : 0;
-    const int words = CELLS + nup + nmac + 1;
+    const int npart = kp.part ? 2 * CELLS : 0;
+    const int nrecv = kp.recv ? 2 * PARTS * recv_entries(BX, BY, BZ) : 0;
+    uint32_t *partw = reinterpret_cast<uint32_t *>(kp.part);
+    uint32_t *recvw = reinterpret_cast<uint32_t *>(kp.recv);
+    const int words = CELLS + nup + nmac + npart + nrecv + 1;
     const size_t total = (size_t)n * words;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
         const int s2 = (int)(e / words), k = (int)(e % words);
@@ -1417,6 +1430,10 @@ __global__ void __launch_bounds__(THREADS) k_sort_aux(KParams kp)
             a = uprev + (size_t)s * nup + (k - CELLS);
         else if (k < CELLS + nup + nmac)
             a = macp + (size_t)s * nmac + (k - CELLS - nup);
+        else if (k < CELLS + nup + nmac + npart)
+            a = partw + (size_t)s * npart + (k - CELLS - nup - nmac);
+        else if (k < CELLS + nup + nmac + npart + nrecv)
+            a = recvw + (size_t)s * nrecv + (k - CELLS - nup - nmac - npart);
         else
             a = reinterpret_cast<uint32_t *>(kp.block_of + s);
         if (BACK) {
@@ -1920,13 +1937,201 @@ __device__ __forceinline__ float2 edot(const float2 *a, const float2 *na)
     return r;
 }
 
+// ---- density partials (FP32, two components, A-B) ----------------------------
+// Pull streaming (Eq. 10, left) makes the density of cell y at step t + 1 the
+// sum of the post-collision values f*_i(y - e_i) of step t (the cell's own
+// f*_opp(i) behind a solid cell, its own stored values at held cells), so
+// the collision of step t already holds every term of it.  Each CTA, once
+// its half block is collided, sums in shared memory
+//   own partial  for each of its cells, the terms that come from the half
+//                block itself (part, one float2 per cell);
+//   entries      for each cell just outside it, the terms it sends there,
+//                stored with the receiving half block (recv).
+// Pass 1 of step t + 1 then adds a cell's own partial and the entries of its
+// faces and edges (Eqs. 4, 6, 7) instead of pulling 38 populations, wherever
+// the warp's 27 blocks are all meshed (or solid); elsewhere, where the
+// criterion needs the velocity too, it pulls as before.  The sums are taken
+// in a fixed order, so every execution mode gives the same bits; they differ
+// from the pull's running sum only by rounding order.
+//
+// The entries of a half block (HX x HY x HZ cells; blocks split in two along
+// z) are grouped by the side they come from: region R has the offset
+// (dx, dy, dz) of the sending half block, faces 0-5 (-x, +x, -y, +y, -z, +z)
+// then the 12 edges; within a region, the receiving cells in x, y, z order
+// over the axes where the offset is 0.
+constexpr int HX = BX, HY = BY, HZ = BZ / PARTS;
+constexpr int NREG = 18;
+// dynamic shared memory of a collision that writes the partials: two
+// buffers of the 19 value pairs of a half block's cells
+constexpr size_t PART_SMEM = 2 * (size_t)Q * THREADS * sizeof(float2);
+static_assert(PARTS == 2, "half blocks along z");
+__host__ __device__ constexpr int reg_dx(int r)
+{
+    return (r == 0 || r == 6 || r == 8 || r == 10 || r == 12) ? -1
+           : (r == 1 || r == 7 || r == 9 || r == 11 || r == 13) ? 1
+                                                                 : 0;
+}
+__host__ __device__ constexpr int reg_dy(int r)
+{
+    return (r == 2 || r == 6 || r == 7 || r == 14 || r == 16) ? -1
+           : (r == 3 || r == 8 || r == 9 || r == 15 || r == 17) ? 1
+                                                                 : 0;
+}
+__host__ __device__ constexpr int reg_dz(int r)
+{
+    return (r == 4 || r == 10 || r == 11 || r == 14 || r == 15) ? -1
+           : (r == 5 || r == 12 || r == 13 || r == 16 || r == 17) ? 1
+                                                                   : 0;
+}
+__host__ __device__ constexpr int reg_size(int r)
+{
+    return (reg_dx(r) == 0 ? HX : 1) * (reg_dy(r) == 0 ? HY : 1) * (reg_dz(r) == 0 ? HZ : 1);
+}
+__host__ __device__ constexpr int reg_base(int r) { return r == 0 ? 0 : reg_base(r - 1) + reg_size(r - 1); }
+constexpr int RECV = reg_base(NREG);
+static_assert(RECV == recv_entries(BX, BY, BZ), "entries per half block");
+
+// Position of a receiving cell (x, y, z; half-block coordinates) in region R.
+template <int R>
+__device__ __forceinline__ int reg_pos(int x, int y, int z)
+{
+    int p = 0, m = 1;
+    if constexpr (reg_dx(R) == 0) { p += x * m; m *= HX; }
+    if constexpr (reg_dy(R) == 0) { p += y * m; m *= HY; }
+    if constexpr (reg_dz(R) == 0) p += z * m;
+    return p;
+}
+// Whether cell (x, y, z) of a half block borders region R.
+template <int R>
+__device__ __forceinline__ bool reg_touch(int x, int y, int z)
+{
+    return (reg_dx(R) == 0 || x == (reg_dx(R) < 0 ? 0 : HX - 1)) &&
+           (reg_dy(R) == 0 || y == (reg_dy(R) < 0 ? 0 : HY - 1)) &&
+           (reg_dz(R) == 0 || z == (reg_dz(R) < 0 ? 0 : HZ - 1));
+}
+// Neighbour-block index (0..26) of the half block at offset (ox, oy, oz),
+// in half blocks, from half h of a block, and that half block's half.
+__device__ __forceinline__ int half_nbr(int ox, int oy, int oz, int h, int &hn)
+{
+    int zh = h + oz, bz = 0;
+    if (zh < 0) {
+        zh += PARTS;
+        bz = -1;
+    } else if (zh >= PARTS) {
+        zh -= PARTS;
+        bz = 1;
+    }
+    hn = zh;
+    return (ox + 1) + 3 * (oy + 1) + 9 * (bz + 1);
+}
+
+// After the collision of half block h of `slot` put every cell's values in
+// sv[i][cell] (post-collision values; zeros at solid cells; the stored
+// values at held cells): this cell's own partial, then the entries this half
+// block sends (a warp-uniform loop; receivers that are unmeshed or solid
+// get none).  All threads of the CTA call, between two barriers.
+__device__ __forceinline__ void part_write(const KParams &kp, const float2 (*sv)[THREADS], int slot,
+                                           int h, int c, uint32_t bits)
+{
+    const int cl = c - h * THREADS;
+    const int lx = lx_of(c), ly = ly_of(c), hz = lz_of(c) - h * HZ;
+    const bool held = (bits >> HELD_BIT) & 1u;
+    const float2 *me = &sv[0][cl];  // sv[i][cl - d] == me[i * THREADS - d]
+    float2 s = me[0];
+    auto one = [&]<int I>() {
+        constexpr int D = cx(I) + HX * (cy(I) + HY * cz(I));  // cell offset of x - e_I
+        const bool inside = (cx(I) == 0 || (cx(I) > 0 ? lx > 0 : lx < HX - 1)) &&
+                            (cy(I) == 0 || (cy(I) > 0 ? ly > 0 : ly < HY - 1)) &&
+                            (cz(I) == 0 || (cz(I) > 0 ? hz > 0 : hz < HZ - 1));
+        if (held)
+            s = add2(s, me[I * THREADS]);
+        else if ((bits >> I) & 1u)
+            s = add2(s, me[opp(I) * THREADS]);
+        else if (inside)
+            s = add2(s, me[I * THREADS - D]);
+    };
+    Unroll<0, NPAIR>::run([&]<int P>() {
+        one.template operator()<pair_rep(P)>();
+        one.template operator()<opp(pair_rep(P))>();
+    });
+    kp.part[(size_t)slot * CELLS + c] = (bits & 1u) ? make_float2(0.f, 0.f) : s;
+    const int *row = kp.nbr + (size_t)slot * NBR_STRIDE;
+    for (int e = threadIdx.x; e < RECV; e += THREADS) {
+        Unroll<0, NREG>::run([&]<int R>() {
+            constexpr int DX = reg_dx(R), DY = reg_dy(R), DZ = reg_dz(R);
+            if (e < reg_base(R) || e >= reg_base(R) + reg_size(R)) return;
+            // the receiving cell, in the receiver's coordinates
+            int p = e - reg_base(R);
+            int x = DX < 0 ? 0 : HX - 1, y = DY < 0 ? 0 : HY - 1, z = DZ < 0 ? 0 : HZ - 1;
+            if constexpr (DX == 0) { x = p % HX; p /= HX; }
+            if constexpr (DY == 0) { y = p % HY; p /= HY; }
+            if constexpr (DZ == 0) z = p;
+            // its sources x - e_i that lie in this half block (at offset
+            // (DX, DY, DZ) from the receiver), in pull order
+            float2 sum = make_float2(0.f, 0.f);
+            Unroll<0, NPAIR>::run([&]<int P>() {
+                Unroll<0, 2>::run([&]<int K>() {
+                    constexpr int I = K == 0 ? pair_rep(P) : opp(pair_rep(P));
+                    if constexpr ((DX == 0 || cx(I) == -DX) && (DY == 0 || cy(I) == -DY) &&
+                                  (DZ == 0 || cz(I) == -DZ)) {
+                        const int sx = x - cx(I) - DX * HX, sy = y - cy(I) - DY * HY, sz = z - cz(I) - DZ * HZ;
+                        if (sx >= 0 && sx < HX && sy >= 0 && sy < HY && sz >= 0 && sz < HZ)
+                            sum = add2(sum, sv[I][sx + HX * (sy + HY * sz)]);
+                    }
+                });
+            });
+            int hn;
+            const int k = half_nbr(-DX, -DY, -DZ, h, hn);
+            const int rs = row[k];
+            if (rs >= 0) kp.recv[((size_t)rs * PARTS + hn) * RECV + e] = sum;
+        });
+    }
+}
+
+// Pass 1 from the partials: the density pair of cell c (not solid, not
+// held) of half block h, from its own partial `own` and the entries of the
+// regions it borders whose sending block exists (bit k of `exist`: block k
+// of the 27 is meshed; unmeshed ones do not occur here, solid ones send
+// nothing because every source in them is solid).
+__device__ __forceinline__ float2 part_gather(const KParams &kp, unsigned exist, int slot, int h, int c,
+                                              float2 own)
+{
+    const int lx = lx_of(c), ly = ly_of(c), hz = lz_of(c) - h * HZ;
+    const float2 *in = kp.recv + ((size_t)slot * PARTS + h) * RECV;
+    float2 rho = own;
+    Unroll<0, NREG>::run([&]<int R>() {
+        int hn;
+        const int k = half_nbr(reg_dx(R), reg_dy(R), reg_dz(R), h, hn);
+        if (reg_touch<R>(lx, ly, hz) && ((exist >> k) & 1u))
+            rho = add2(rho, in[reg_base(R) + reg_pos<R>(lx, ly, hz)]);
+    });
+    return rho;
+}
+
+// Pass 1 of one cell from the partials: mac (densities and psi, Eqs. 4, 6,
+// 7) from the own partial and, for cells neither solid nor held, the
+// entries (held cells pull only their own values).  row: this lane's entry
+// of the slot's neighbour row; every lane of the warp calls.
+__device__ __forceinline__ void part_mac(const KParams &kp, int slot, int c, int row, uint32_t bits, float2 own)
+{
+    const unsigned exist = __ballot_sync(FULL, row >= 0);
+    const bool live = !(bits & 1u);
+    float2 rho = own;
+    if (live && !((bits >> HELD_BIT) & 1u)) rho = part_gather(kp, exist, slot, c / THREADS, c, rho);
+    kp.mac[(size_t)slot * CELLS + c] =
+        live ? mac_pack(rho.x, psi_of(kp, rho.x), rho.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 // One work item of pass 1, FP32 form with two components, paired
 // arithmetic (as k_macro): streaming and moments of the cells c of one half
 // block (row: the slot's neighbour-table entry of this lane, bits: the
 // cell's solid word); with `criterion`, Eq. 13 at cells bordering unmeshed
 // blocks.  par, n: the step's parity and meshed count.  CG: the populations
-// and previous velocities were written earlier in the same launch.  All
-// lanes of the warp call.
+// and previous velocities were written earlier in the same launch.
+// part_in: the densities come from the partials the previous collision
+// wrote, in warps whose 27 blocks are all meshed or solid (own_part: the
+// cell's own partial, loaded ahead by the caller).  All lanes of the warp
+// call.
 // Called by the item functions once the pull's loads are consumed (the
 // fused step publishes the previous item's completion there).
 struct NoHook {
@@ -1936,6 +2141,7 @@ struct NoHook {
 template <bool CG, class Hook = NoHook>
 __device__ __forceinline__ void macro2_item(const KParams &kp, Ctrl *ctrl, const float *rd, int par, int n,
                                             int slot, int c, int row, uint32_t bits, int criterion,
+                                            bool part_in = false, float2 own_part = float2{},
                                             Hook &&hook = Hook{})
 {
     const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
@@ -1944,6 +2150,11 @@ __device__ __forceinline__ void macro2_item(const KParams &kp, Ctrl *ctrl, const
     const bool held = (bits >> HELD_BIT) & 1u;
     if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 2))) {
         hook();
+        return;
+    }
+    if (part_in && wn.amb == 0u) {  // warp-uniform
+        hook();
+        part_mac(kp, slot, c, row, bits, own_part);
         return;
     }
     if (!criterion || wn.amb == 0u) {
@@ -1978,7 +2189,7 @@ __device__ __forceinline__ void macro2_item(const KParams &kp, Ctrl *ctrl, const
 
 // Pass 1 of a step, FP32 form with two components (grid-stride over the
 // half-block items of the meshed slots).
-__device__ __forceinline__ void macro2_body(const KParams &kp, int step, int criterion)
+__device__ __forceinline__ void macro2_body(const KParams &kp, int step, int criterion, bool part_in)
 {
     Ctrl *ctrl = kp.ctrl;
     if (criterion && ctrl->status) return;
@@ -1988,54 +2199,130 @@ __device__ __forceinline__ void macro2_body(const KParams &kp, int step, int cri
     const float *rd = kp.f + (size_t)par * kp.buf_stride;
     const int total = n * PARTS;
     int it = blockIdx.x;
+    // the next item's table row, solid word and (with the partials) own
+    // partial are loaded one item ahead
+    auto cell_of = [&](int i) { return (size_t)(i / PARTS) * CELLS + (i % PARTS) * THREADS + threadIdx.x; };
     int next_row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
-    uint32_t next_bits =
-        it < total ? kp.nbits[(size_t)(it / PARTS) * CELLS + (it % PARTS) * THREADS + threadIdx.x] : 1u;
+    uint32_t next_bits = it < total ? kp.nbits[cell_of(it)] : 1u;
+    float2 next_part = part_in && it < total ? kp.part[cell_of(it)] : make_float2(0.f, 0.f);
     for (; it < total; it += gridDim.x) {
         const int slot = it / PARTS;
         const int c = (it % PARTS) * THREADS + threadIdx.x;
         const int row = next_row;
         const uint32_t bits = next_bits;
+        const float2 own_part = next_part;
         const int it2 = it + gridDim.x;
         if (it2 < total) {
             next_row = nbr_row_lane(kp, it2 / PARTS);
-            next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
+            next_bits = kp.nbits[cell_of(it2)];
+            if (part_in) next_part = kp.part[cell_of(it2)];
         }
-        macro2_item<false>(kp, ctrl, rd, par, n, slot, c, row, bits, criterion);
+        macro2_item<false>(kp, ctrl, rd, par, n, slot, c, row, bits, criterion, part_in, own_part);
     }
 }
 
 __global__ void __launch_bounds__(THREADS, 3) k_macro2(KParams kp, int criterion)
 {
     const int step = kp.ctrl->step;
-    macro2_body(kp, step, criterion);
+    macro2_body(kp, step, criterion, kp.part_in != 0);
+    if (criterion) order_tail(kp, step);
+}
+
+// Pass 1 split in two launches when the partials are there (FP32, two
+// components, A-B).  k_macro2p: the warps whose 27 blocks are all meshed or
+// solid, from the partials; a light kernel (few registers, many warps in
+// flight, the next item's table row loaded ahead).  k_macro2f: the other
+// warps (they border an unmeshed block, so only a progressive mesh has
+// them), pulled as in k_macro2 with the criterion; its last CTA renumbers
+// the candidates.  Together they write what one k_macro2 launch with
+// kp.part_in writes, bit for bit.
+__global__ void __launch_bounds__(THREADS, 6) k_macro2p(KParams kp)
+{
+    const Ctrl *ctrl = kp.ctrl;
+    const int par = ctrl->step & 1;
+    const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int it2 = it + gridDim.x;
+        const int next_row = it2 < total ? nbr_row_lane(kp, it2 / PARTS) : SOLIDBLK;
+        const unsigned amb = __ballot_sync(FULL, row == AMBIENT) & ~(1u << 13);
+        const bool ok = __all_sync(FULL, in_range(kp, row + 2, (long long)kp.capacity + 2, 2));
+        if (amb == 0u && ok) {
+            const size_t cell = (size_t)slot * CELLS + c;
+            part_mac(kp, slot, c, row, kp.nbits[cell], kp.part[cell]);
+        }
+        row = next_row;
+    }
+}
+
+__device__ __forceinline__ void macro2_frontier_body(const KParams &kp, int step, int criterion)
+{
+    Ctrl *ctrl = kp.ctrl;
+    if (criterion && ctrl->status) return;
+    const int par = step & 1;
+    const int n = ctrl->n_active[par];
+    if (!in_range(kp, n, (long long)kp.capacity + 1, 1)) return;
+    const float *rd = kp.f + (size_t)par * kp.buf_stride;
+    const int total = n * PARTS;
+    int it = blockIdx.x;
+    int row = it < total ? nbr_row_lane(kp, it / PARTS) : SOLIDBLK;
+    for (; it < total; it += gridDim.x) {
+        const int slot = it / PARTS;
+        const int c = (it % PARTS) * THREADS + threadIdx.x;
+        const int it2 = it + gridDim.x;
+        const int next_row = it2 < total ? nbr_row_lane(kp, it2 / PARTS) : SOLIDBLK;
+        if (__ballot_sync(FULL, row == AMBIENT) & ~(1u << 13))  // warp-uniform
+            macro2_item<false>(kp, ctrl, rd, par, n, slot, c, row, kp.nbits[(size_t)slot * CELLS + c],
+                               criterion);
+        row = next_row;
+    }
+}
+
+__global__ void __launch_bounds__(THREADS, 3) k_macro2f(KParams kp, int criterion)
+{
+    const int step = kp.ctrl->step;
+    macro2_frontier_body(kp, step, criterion);
     if (criterion) order_tail(kp, step);
 }
 
 // One work item of pass 2, FP32 form with two components, paired
 // arithmetic (as k_collide): streaming again, forces from the neighbours'
 // mac, forced BGK collision into the write buffer, the velocity kept at
-// cells bordering unmeshed blocks.  All lanes of the warp call.
-template <bool TAU1, class Hook = NoHook>
+// cells bordering unmeshed blocks.  PART: also every cell's values in
+// sv[i][cell of the half block] for the density partials.  All lanes of the
+// warp call.
+template <bool TAU1, bool PART = false, class Hook = NoHook, class Mid = NoMid>
 __device__ __forceinline__ void collide2_item(const KParams &kp, const float *rd, float *wr, int slot, int c,
-                                              int row, uint32_t bits, Hook &&hook = Hook{})
+                                              int row, uint32_t bits, float2 (*sv)[THREADS] = nullptr,
+                                              Hook &&hook = Hook{}, Mid &&mid = Mid{})
 {
     const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
     const WarpNbr wn = warp_nbr_of(kp, row);
-    const bool live = !(bits & 1u) && !((bits >> HELD_BIT) & 1u);
+    const bool held = (bits >> HELD_BIT) & 1u;
+    const bool live = !(bits & 1u) && !held;
+    const int cl = c & (THREADS - 1);
     // every lane takes part in the ballot (it must not sit behind &&)
     const bool row_live = row_has(live);
     const bool fill = (bits & 1u) && row_live;  // solid cell completing a sector
     if (!__all_sync(FULL, in_range(kp, wn.slot + 2, (long long)kp.capacity + 2, 8))) {
         hook();
+        mid();
         return;
     }
     Moments2 m;
     float2 fin[TAU1 ? 1 : Q];
-    pull2_f32(kp, wn, rd, slot, c, lx, ly, lz, bits, live, [&]<int I>(float2 v) {
-        m.template add<I>(v);
-        if constexpr (!TAU1) fin[I] = v;
-    });
+    pull2_f32(
+        kp, wn, rd, slot, c, lx, ly, lz, bits, live,
+        [&]<int I>(float2 v) {
+            m.template add<I>(v);
+            if constexpr (!TAU1) fin[I] = v;
+        },
+        mid);
     hook();
     const float2 rho = m.rho;
     const float2 inv = make_float2(1.f / rho.x, 1.f / rho.y);
@@ -2044,6 +2331,16 @@ __device__ __forceinline__ void collide2_item(const KParams &kp, const float *rd
     for (int d = 0; d < 3; ++d) u[d] = mul2(m.j[d], inv);
     float2 F[3];
     forces2<2>(kp, wn, 0u, slot, c, lx, ly, lz, bits, live, rho, F);
+    if constexpr (PART) {
+        if (held) {  // its stored values, which its neighbours pull
+            const float *own = rd + (size_t)slot * kp.slot_floats + c;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) sv[i][cl] = make_float2(own[i * CELLS], own[(Q + i) * CELLS]);
+        } else if (!live && !fill) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) sv[i][cl] = make_float2(0.f, 0.f);
+        }
+    }
     if (!live && !fill) return;
     float2 v[3], nv[3], nu[3];
 #pragma unroll
@@ -2077,10 +2374,12 @@ __device__ __forceinline__ void collide2_item(const KParams &kp, const float *rd
         moving = add2(moving, f);
         d0[I * CELLS] = live ? f.x : 0.f;
         d1[I * CELLS] = live ? f.y : 0.f;
+        if constexpr (PART) sv[I][cl] = live ? f : make_float2(0.f, 0.f);
     });
     const float2 rest = sub2(rho, moving);
     d0[0] = live ? rest.x : 0.f;
     d1[0] = live ? rest.y : 0.f;
+    if constexpr (PART) sv[0][cl] = live ? rest : make_float2(0.f, 0.f);
     (void)cu;
     if (live && kp.progressive && (reach_bits(lx, ly, lz) & wn.amb)) {
         float *up = kp.uprev + (size_t)slot * 2 * 3 * CELLS + c;
@@ -2093,10 +2392,17 @@ __device__ __forceinline__ void collide2_item(const KParams &kp, const float *rd
 }
 
 // Pass 2 of a step, FP32 form with two components (grid-stride over the
-// half-block items).
-template <bool TAU1>
+// half-block items); PART: with the density partials of the next step (the
+// launch then gives PART_SMEM bytes of dynamic shared memory).
+template <bool TAU1, bool PART = false>
 __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
 {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int buf = 0, prev_slot = -1, prev_h = 0;
+    uint32_t prev_bits = 0;
+    (void)buf;
+    (void)prev_h;
+    (void)prev_bits;
     Ctrl *ctrl = kp.ctrl;
     if (ctrl->status) return;
     const int par = step & 1;
@@ -2123,15 +2429,42 @@ __device__ __forceinline__ void collide2_body(const KParams &kp, int step)
             next_row = nbr_row_lane(kp, it2 / PARTS);
             next_bits = kp.nbits[(size_t)(it2 / PARTS) * CELLS + (it2 % PARTS) * THREADS + threadIdx.x];
         }
-        collide2_item<TAU1>(kp, rd, wr, slot, c, row, bits);
+        if constexpr (PART) {
+            // Two buffers of PART_SMEM / 2 bytes, alternating by item.  The
+            // partial sums of an item run in the next item's collision,
+            // after its loads are issued (their latency hides them), past
+            // a barrier that every warp reaches only once it has written
+            // the item's values and finished the sums of the item before,
+            // which used the buffer this item writes.
+            float2 (*base)[THREADS] = reinterpret_cast<float2 (*)[THREADS]>(smem_raw);
+            float2 (*sv)[THREADS] = base + (size_t)buf * Q;
+            float2 (*pv)[THREADS] = base + (size_t)(buf ^ 1) * Q;
+            auto mid = [&]() {
+                __syncthreads();
+                if (prev_slot >= 0) part_write(kp, pv, prev_slot, prev_h, prev_h * THREADS + threadIdx.x, prev_bits);
+            };
+            collide2_item<TAU1, true>(kp, rd, wr, slot, c, row, bits, sv, NoHook{}, mid);
+            prev_slot = slot;
+            prev_h = it % PARTS;
+            prev_bits = bits;
+            buf ^= 1;
+        } else {
+            collide2_item<TAU1>(kp, rd, wr, slot, c, row, bits);
+        }
+    }
+    if constexpr (PART) {  // the sums of the last item
+        __syncthreads();
+        if (prev_slot >= 0)
+            part_write(kp, reinterpret_cast<float2 (*)[THREADS]>(smem_raw) + (size_t)(buf ^ 1) * Q, prev_slot,
+                       prev_h, prev_h * THREADS + threadIdx.x, prev_bits);
     }
 }
 
-template <bool TAU1>
+template <bool TAU1, bool PART>
 __global__ void __launch_bounds__(THREADS, 2) k_collide2(KParams kp)
 {
     const int step = *(volatile const int *)&kp.ctrl->step;
-    collide2_body<TAU1>(kp, step);
+    collide2_body<TAU1, PART>(kp, step);
     step_done(kp.ctrl, step);
 }
 
@@ -2286,7 +2619,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused2(KParams kp)
             return;
         }
         macro2_item<true>(kp, ctrl, wr, par ^ 1, n, idx / PARTS, (idx % PARTS) * THREADS + tid, row, bits,
-                          kp.progressive, hook);
+                          kp.progressive, false, float2{}, hook);
     };
 
     const int total = 2 * C;
@@ -2332,7 +2665,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_fused2(KParams kp)
         if (__shfl_sync(FULL, *(volatile int *)&ctrl->status, 0) != 0) continue;
         if (kind == FZ_COLLIDE) {
             if (tid == 0) cnt_next[idx] = 0;
-            collide2_item<TAU1>(kp, rd, wr, idx / PARTS, (idx % PARTS) * THREADS + tid, row, bits, hook);
+            collide2_item<TAU1>(kp, rd, wr, idx / PARTS, (idx % PARTS) * THREADS + tid, row, bits, nullptr,
+                                hook);
             pending = idx;
         } else if (fz_far(__reduce_max_sync(FULL, row), q, L)) {
             if (tid == 0) ++deferred;  // redone below (lane 13 of row holds the slot itself)
@@ -3267,29 +3601,35 @@ __device__ __forceinline__ bool grid_sync(Ctrl *ctrl, unsigned expect, long long
 template <int NC, bool TAU1, int ST>
 struct Phases {
     static constexpr int MIN_CTAS = Store<ST>::DEV ? DEV_COLLIDE_MIN_CTAS : 2;
-    __device__ __forceinline__ static void macro(const KParams &kp, int step, int crit)
+    __device__ __forceinline__ static void macro(const KParams &kp, int step, int crit, bool part_in)
     {
         if constexpr (Store<ST>::DEV)
             macro_dev_body<NC, ST>(kp, step, crit);
         else if constexpr (NC == 2)
-            macro2_body(kp, step, crit);
+            macro2_body(kp, step, crit, part_in);
         else
             macro_body<NC>(kp, step, crit);
     }
     __device__ __forceinline__ static void collide(const KParams &kp, int step)
     {
-        if constexpr (Store<ST>::DEV)
+        if constexpr (Store<ST>::DEV) {
             collide_dev_body<NC, TAU1, ST>(kp, step);
-        else if constexpr (NC == 2)
-            collide2_body<TAU1>(kp, step);
-        else
+        } else if constexpr (NC == 2) {
+            if (kp.part_out)
+                collide2_body<TAU1, true>(kp, step);
+            else
+                collide2_body<TAU1>(kp, step);
+        } else {
             collide_body<NC, TAU1>(kp, step);
+        }
     }
 };
 
 // nsteps steps: stream + moments (+ criterion), grid barrier, block
 // creation, barrier, forces + collision, barrier; the same bodies as the
-// per-phase launches, so the results are the same bit for bit.
+// per-phase launches, so the results are the same bit for bit.  The first
+// pass 1 sums the density partials when kp.part_in says they are there,
+// the others when the collisions write them (kp.part_out).
 template <int NC, bool TAU1, int ST>
 __global__ void __launch_bounds__(THREADS, (Phases<NC, TAU1, ST>::MIN_CTAS)) k_run(KParams kp, int nsteps,
                                                                               int progressive)
@@ -3298,7 +3638,7 @@ __global__ void __launch_bounds__(THREADS, (Phases<NC, TAU1, ST>::MIN_CTAS)) k_r
     Ctrl *ctrl = kp.ctrl;
     int step = *(volatile int *)&ctrl->step;
     for (int k = 0; k < nsteps; ++k, ++step) {
-        P::macro(kp, step, progressive);
+        P::macro(kp, step, progressive, k == 0 ? kp.part_in != 0 : kp.part_out != 0);
         if (!grid_sync(ctrl, gridDim.x, kp.barrier_spins)) return;
         if (progressive) {
             if (blockIdx.x == 0) order_body(kp, step);
@@ -3314,14 +3654,16 @@ __global__ void __launch_bounds__(THREADS, (Phases<NC, TAU1, ST>::MIN_CTAS)) k_r
 
 // ---- launch wrappers of one storage form -------------------------------------
 
-// Resident CTAs per SM of a kernel, looked up once per process.
-template <auto Kern>
+// Resident CTAs per SM of a kernel with SMEM bytes of dynamic shared
+// memory (opted in above the default 48 KB), looked up once per process.
+template <auto Kern, size_t SMEM = 0>
 int occupancy()
 {
     static int cached = 0;
     if (!cached) {
+        if (SMEM > 48 * 1024) cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Kern, THREADS, 0) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, Kern, THREADS, SMEM) != cudaSuccess) {
             cudaGetLastError();
             n = 1;
         }
@@ -3330,10 +3672,10 @@ int occupancy()
     return cached;
 }
 
-template <auto Kern, class... A>
+template <auto Kern, size_t SMEM = 0, class... A>
 cudaError_t launch_persistent(int sms, cudaStream_t s, A... args)
 {
-    Kern<<<sms * occupancy<Kern>(), THREADS, 0, s>>>(args...);
+    Kern<<<sms * occupancy<Kern, SMEM>(), THREADS, SMEM, s>>>(args...);
     return cudaGetLastError();
 }
 
@@ -3402,6 +3744,11 @@ struct Launch {
         } else {
             if (kp.aa) return launch_persistent<k_macro_aa>(sms, s, kp, criterion);
             if (kp.ncomp == 2 && kp.staged) return launch_staged<k_macro2_staged>(sms, s, kp, criterion);
+            if (kp.ncomp == 2 && kp.part_in) {
+                cudaError_t e = launch_persistent<k_macro2p>(sms, s, kp);
+                if (e == cudaSuccess && kp.progressive) e = launch_persistent<k_macro2f>(sms, s, kp, criterion);
+                return e;
+            }
             if (kp.ncomp == 2) return launch_persistent<k_macro2>(sms, s, kp, criterion);
             return launch_persistent<k_macro<1>>(sms, s, kp, criterion);
         }
@@ -3434,9 +3781,13 @@ struct Launch {
                 if (tau1) return launch_staged<k_collide2_staged<true>>(sms, s, kp);
                 return launch_staged<k_collide2_staged<false>>(sms, s, kp);
             }
+            if (kp.ncomp == 2 && kp.part_out) {
+                if (tau1) return launch_persistent<k_collide2<true, true>, PART_SMEM>(sms, s, kp);
+                return launch_persistent<k_collide2<false, true>, PART_SMEM>(sms, s, kp);
+            }
             if (kp.ncomp == 2) {
-                if (tau1) return launch_persistent<k_collide2<true>>(sms, s, kp);
-                return launch_persistent<k_collide2<false>>(sms, s, kp);
+                if (tau1) return launch_persistent<k_collide2<true, false>>(sms, s, kp);
+                return launch_persistent<k_collide2<false, false>>(sms, s, kp);
             }
             if (tau1) return launch_persistent<k_collide<1, true>>(sms, s, kp);
             return launch_persistent<k_collide<1, false>>(sms, s, kp);
@@ -3475,10 +3826,14 @@ struct Launch {
     static cudaError_t run_on(const KParams &kp, int nsteps, int progressive, int sms, cudaStream_t s)
     {
         auto kern = k_run<NC, TAU1, ST>;
-        const int grid = sms * occupancy<k_run<NC, TAU1, ST>>();
+        // (the grid fits the residency with the partials' shared memory,
+        // whether or not this launch writes them)
+        constexpr size_t RUN_SMEM = !Store<ST>::DEV && NC == 2 ? PART_SMEM : 0;
+        const int grid = sms * occupancy<k_run<NC, TAU1, ST>, RUN_SMEM>();
         KParams a = kp;
         void *args[] = {&a, &nsteps, &progressive};
-        return cudaLaunchCooperativeKernel((const void *)kern, grid, THREADS, args, 0, s);
+        return cudaLaunchCooperativeKernel((const void *)kern, grid, THREADS, args, kp.part_out ? RUN_SMEM : 0,
+                                           s);
     }
     static cudaError_t run(const KParams &kp, int nsteps, int progressive, int sms, cudaStream_t s)
     {
@@ -3498,7 +3853,7 @@ struct Launch {
             a = occupancy<k_collide_dev<2, true, ST>>();
             b = occupancy<k_macro_dev<2, ST>>();
         } else {
-            a = occupancy<k_collide2<true>>();
+            a = occupancy<k_collide2<true, true>, PART_SMEM>();
             b = occupancy<k_macro2>();
         }
         return a < b ? a : b;

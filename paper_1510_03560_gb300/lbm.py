@@ -73,7 +73,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_set_geometry", "lbm_step", "lbm_ste
            "lbm_mlp_create", "lbm_mlp_destroy", "lbm_mlp_set_params", "lbm_mlp_get_params",
            "lbm_mlp_set_scaling", "lbm_mlp_forward", "lbm_mlp_loss_grad", "lbm_mlp_adam",
            "lbm_set_proposer", "lbm_set_exec", "lbm_barrier_selftest", "lbm_set_slot_order",
-           "lbm_set_slot_strip", "lbm_set_fusion"]
+           "lbm_set_slot_strip", "lbm_set_fusion", "lbm_set_density_partials"]
 NOALLOC_MAX_BLOCKS = 65536
 MLP_IN, MLP_HIDDEN = 34, 64
 MLP_NPARAM = MLP_IN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + 2 * MLP_HIDDEN + 1
@@ -129,6 +129,7 @@ def load():
     lib.lbm_set_slot_order.argtypes = [vp, C.c_int]
     lib.lbm_set_slot_strip.argtypes = [vp, C.c_int]
     lib.lbm_set_fusion.argtypes = [vp, C.c_int, C.c_int]
+    lib.lbm_set_density_partials.argtypes = [vp, C.c_int]
     for name in EXPORTS:
         if name != "lbm_last_error":
             getattr(lib, name).restype = C.c_int
@@ -199,8 +200,9 @@ class LBM:
     torch.cuda.Stream (default: the current stream).  ``torch_alloc``:
     allocate through torch's caching allocator (default) or let the library
     use cudaMallocAsync.  ``slot_strip`` (lbm_set_slot_strip, before the
-    geometry) and ``fusion`` = (on, max_lag) (lbm_set_fusion) are applied
-    right after the context is created when given.
+    geometry), ``fusion`` = (on, max_lag) (lbm_set_fusion) and ``partials``
+    (lbm_set_density_partials) are applied right after the context is
+    created when given.
     """
 
     def __init__(self, stream=None, torch_alloc=True, **kw):
@@ -251,6 +253,7 @@ class LBM:
         p.max_blocks = int(kw.get("max_blocks", 0))
         strip = kw.get("slot_strip", None)
         fusion = kw.get("fusion", None)
+        partials = kw.get("partials", None)
         self._alloc = None
         if torch_alloc:
             self._alloc = _TorchAllocator(torch, self.device, self.torch_stream.cuda_stream)
@@ -267,6 +270,8 @@ class LBM:
             self.set_slot_strip(strip)
         if fusion is not None:
             self.set_fusion(*fusion)
+        if partials is not None:
+            self.set_density_partials(partials)
 
     # -- lifetime
     def close(self):
@@ -403,8 +408,15 @@ def _lbm_set_fusion(self, on: bool = True, max_lag: int = 0):
     self._check(self.lib.lbm_set_fusion(self.h, 1 if on else 0, int(max_lag)))
 
 
+def _lbm_set_density_partials(self, on: bool = True):
+    """Pass 1 sums the densities the collision prepared instead of pulling
+    (lbm_set_density_partials)."""
+    self._check(self.lib.lbm_set_density_partials(self.h, 1 if on else 0))
+
+
 LBM.set_slot_strip = _lbm_set_slot_strip
 LBM.set_fusion = _lbm_set_fusion
+LBM.set_density_partials = _lbm_set_density_partials
 LBM.frontier_features = _lbm_frontier_features
 LBM.activation_steps = _lbm_activation_steps
 LBM.set_proposer = _lbm_set_proposer

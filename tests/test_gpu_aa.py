@@ -63,7 +63,7 @@ def _compare(ab, aa, case):
 @pytest.mark.parametrize("which", sorted(CASES))
 def test_aa_equals_ab_bit_for_bit(L, which):
     case = CASES[which]()
-    ab = L.from_case(case)
+    ab = L.from_case(case, partials=False)  # A-A pulls in every pass 1
     aa = L.from_case(case, streaming="aa")
     _compare(ab, aa, case)  # the initial layout
     for n in CHUNKS:
@@ -142,7 +142,7 @@ def test_aa_pool_exhaustion_keeps_last_complete_step(L):
     collision never ran), equal to the A-B run stopped there."""
     case = W.drop_in_box()
     small = L.from_case(case, streaming="aa", max_blocks=12)
-    ref = L.from_case(case)
+    ref = L.from_case(case, partials=False)
     failed_at = None
     for t in range(40):
         try:

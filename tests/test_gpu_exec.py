@@ -2,7 +2,9 @@
 CUDA graph of two steps, and as one cooperative launch per call with grid
 barriers.  All run the same per-cell code, so results must agree bit for
 bit; the barrier's bounded wait is checked with a barrier that cannot
-complete."""
+complete.  (These run with the density partials off, the default; the
+TMA-staged kernels have none.  tests/test_gpu_partials.py compares the
+modes with them on.)"""
 import numpy as np
 import pytest
 

@@ -7,7 +7,8 @@ end of the launch, or all collisions first), the slot order (block order or
 strips of block rows), the execution mode, the block shape and the points
 where the slots are renumbered.  Between calls the next step's pass 1 has
 already run; every query must still see the state of the last completed
-step."""
+step.  The fused step's pass 1 pulls, so every run here has the density
+partials off."""
 import numpy as np
 import pytest
 
@@ -50,7 +51,8 @@ def _assert_same(a, b, ct, label):
 
 def _run(L, case, chunks, fusion, mode="stream", strip=None, sort=64, **over):
     # (the strip order is set before from_case applies the geometry)
-    sim = L.from_case(case, fusion=fusion, **({} if strip is None else {"slot_strip": strip}), **over)
+    sim = L.from_case(case, fusion=fusion, partials=False,
+                     **({} if strip is None else {"slot_strip": strip}), **over)
     sim.set_exec(mode)
     sim.set_slot_order(sort)
     out = []
@@ -121,7 +123,7 @@ def test_modes_with_fusion_on(L, mode):
     and repeat a pass 1 that ran ahead (its marks are idempotent)."""
     case = _porous()
     ref, _ = _run(L, case, CHUNKS, (False, 0), sort=8)
-    sim = L.from_case(case, fusion=(True, 0))
+    sim = L.from_case(case, fusion=(True, 0), partials=False)
     sim.set_slot_order(8)
     got = []
     for k, n in enumerate(CHUNKS):
@@ -141,7 +143,7 @@ def test_block_shapes(L, block):
                               S=1e-4, block=block)
     out = []
     for fusion in ((False, 0), (True, 0)):
-        sim = L.from_case(case, fusion=fusion)
+        sim = L.from_case(case, fusion=fusion, partials=False)
         sim.step(30)
         out.append((sim.active_blocks(), [np.stack(sim.macro(a)) for a in range(2)], sim.mass()))
         sim.close()
@@ -156,8 +158,8 @@ def test_queries_between_calls(L):
     they are not meshed yet for any query, and stepping on gives the same
     result as an unfused run."""
     case = W.drop_in_box()
-    ref = L.from_case(case, fusion=(False, 0))
-    sim = L.from_case(case, fusion=(True, 0))
+    ref = L.from_case(case, fusion=(False, 0), partials=False)
+    sim = L.from_case(case, fusion=(True, 0), partials=False)
     created = False
     for t in range(40):
         ref.step(1)
