@@ -162,6 +162,10 @@ typedef struct lbm_stats {
 /* Validate `p`, allocate the block pool (capacity x 2 buffers x ncomp x 19 x
  * 512 populations of 4 bytes, or 2 in the 16-bit storage forms; one buffer
  * with A-A streaming) and the tables, and return a new context in *out.
+ * The pool holds the sub-domains of Sec. 4.1 (here 8^3-cell blocks, or the
+ * other block shapes): the domain is not meshed all at once, blocks are
+ * taken from the pool as the fluid reaches them (Sec. 4.2-4.3), and
+ * max_blocks bounds how many can exist (Fig. 3).
  * Allocates through p->dev_alloc when given.  Errors: LBM_EINVAL (bad
  * parameter: grid not a multiple of 8, ncomp not 1 or 2, tau <= 0.5, S < 0,
  * unknown storage form or streaming pattern, A-A streaming without the FP32
@@ -169,7 +173,8 @@ typedef struct lbm_stats {
  * LBM_ECUDA.  On error *out is NULL. */
 int lbm_create(const lbm_params *p, lbm_ctx **out);
 
-/* Free everything the context holds.  NULL is accepted. */
+/* Free everything the context holds (the sub-domain pool of Sec. 4.1 and
+ * its tables).  Waits for the context's stream first.  NULL is accepted. */
 int lbm_destroy(lbm_ctx *ctx);
 
 /* Geometry and initial state (Sec. 4.1: the first sub-domains are created
@@ -216,13 +221,22 @@ int lbm_sync(lbm_ctx *ctx);
  * of the four may be NULL).  Errors: LBM_EINVAL, LBM_ESTATE, LBM_ECUDA. */
 int lbm_get_macro(lbm_ctx *ctx, int comp, float *rho, float *ux, float *uy, float *uz);
 
-/* Ids of the meshed blocks in ascending order.  Writes min(n, cap) ids to
- * `ids` (host, may be NULL when cap is 0) and the count to *n. */
+/* Ids of the meshed blocks in ascending order: the sub-domains created so
+ * far (Sec. 4.1, Fig. 3: the first ones at lbm_set_geometry, then those the
+ * criterion of Eq. 13 added, Sec. 4.3).  Block id = bx + nbx (by + nby bz).
+ * Writes min(n, cap) ids to `ids` (host, may be NULL when cap is 0) and the
+ * count to *n (cap <= 0 writes no ids).  Errors: LBM_EINVAL (ctx or n NULL,
+ * or ids NULL with cap > 0), LBM_ESTATE (no geometry), LBM_ECUDA. */
 int lbm_active_blocks(lbm_ctx *ctx, int32_t *ids, long long cap, long long *n);
 
-/* Per-component mass, the sum of the populations over every non-solid
- * cell, unmeshed cells counted at the ambient equilibrium; accumulated in
- * FP64 on the device in a fixed order.  mass: host array of ncomp doubles. */
+/* Per-component mass: the density of Eq. 4 (the sum of a cell's
+ * populations) summed over every non-solid cell, unmeshed cells counted at
+ * the ambient equilibrium.  Streaming, bounce-back and the collision's
+ * rest population (taken from the mass balance) conserve it, so it is the
+ * check of a run: accumulated in FP64 on the device, per block and then
+ * over blocks in slot order, so the same state gives the same bits.  mass:
+ * host array of ncomp doubles.  Errors: LBM_EINVAL, LBM_ESTATE (no
+ * geometry), LBM_ECUDA. */
 int lbm_mass(lbm_ctx *ctx, double *mass);
 
 /* Post-collision populations of one meshed block, host array
