@@ -183,7 +183,7 @@ def sample_steps(total, warmup, k):
 
 
 def run_timed(L, torch, case, sample, total, progressive, flush, uuid, storage="fp32", proposer=None,
-              exec_mode="stream", streaming="ab", slot_order=64, partials=True):
+              exec_mode="stream", streaming="ab", slot_order=64, partials=False):
     """Run the whole trajectory of `total` steps, timing the steps listed in
     `sample` one by one (L2 flushed before each, a synchronize on both
     sides); the device time of the whole trajectory is recorded too.
