@@ -438,6 +438,9 @@ def main():
                     help="length of the trajectory every run goes through (the workload's 5000 steps)")
     ap.add_argument("--fusion", default="off", choices=["on", "off"],
                     help="collision and the next step's pass 1 in one launch (FP32, two components, A-B)")
+    ap.add_argument("--partials", default="off", choices=["on", "off"],
+                    help="density partials: the collision sums the next step's densities, pass 1 adds "
+                         "them instead of pulling (FP32, two components, A-B)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--S", type=float, default=None, help="criterion threshold override")
     ap.add_argument("--no-static", action="store_true")
@@ -489,7 +492,7 @@ def main():
     sample = sample_steps(args.total, args.warmup, args.steps)
     if args.static_only:
         st = run_timed(L, torch, case, sample, args.total, 0, flush, uuid, args.storage,
-                       exec_mode=args.exec, streaming=args.streaming)
+                       exec_mode=args.exec, streaming=args.streaming, partials=args.partials == "on")
         if rank == 0:
             print(json.dumps({"static_mlups": st["cells"] / (st["ms"] * 1e-3) / 1e6,
                               "ms": st["ms"], "kernel_ms": st["kernel_ms"],
@@ -500,7 +503,8 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     prog = run_timed(L, torch, case, sample, args.total, 1, flush, uuid, args.storage,
-                     exec_mode=args.exec, streaming=args.streaming, slot_order=args.slot_order)
+                     exec_mode=args.exec, streaming=args.streaming, slot_order=args.slot_order,
+                     partials=args.partials == "on")
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -509,7 +513,7 @@ def main():
     stat = None
     if not args.no_static:
         stat = run_timed(L, torch, case, sample, args.total, 0, flush, uuid, args.storage,
-                         streaming=args.streaming)
+                         streaming=args.streaming, partials=args.partials == "on")
         s_max, s_cells = reduce_max_sum(dist, torch, stat["ms"], stat["cells"])
     forms = {}
 
@@ -592,6 +596,7 @@ def main():
         "mode": "progressive", "grid": [case["params"][k] for k in ("nx", "ny", "nz")],
         "block": list(case["params"]["block"]),
         "storage": args.storage, "exec": args.exec, "streaming": args.streaming, "fusion": args.fusion,
+        "density_partials": args.partials,
         "slot_order_period": args.slot_order, "slot_sorts": prog["slot_sorts"],
         "S": case["params"]["S"],
         "trajectory_steps": args.total, "timed_steps": sample,
