@@ -132,10 +132,14 @@ def test_async_steps_match_synchronous(L):
     assert st["steps"] == 30 and st["cell_updates"] > 0
 
 
-def one_step_sample(L, gpu, case, block_ids):
+def one_step_sample(L, gpu, case, block_ids, rho_tol=None):
     """For each sampled block whose 26 neighbours are all meshed: rebuild its
     3 x 3 x 3-block neighbourhood in the oracle from the library's current
-    populations, advance one step on both, compare the centre block."""
+    populations, advance one step on both, compare the centre block.  FP32:
+    each population within 2e-5 relative.  16-bit forms (rho_tol): each
+    population within rho_tol x the cell's density (the one rounding of the
+    stored deviation; the inputs are the same decoded values on both
+    sides)."""
     nx, ny, nz = (case["params"][k] for k in ("nx", "ny", "nz"))
     omap = order_map(L)
     before = {}
@@ -170,8 +174,14 @@ def one_step_sample(L, gpu, case, block_ids):
             want = orc.get_f(a)[8:16, 8:16, 8:16][..., omap]  # [z][y][x][dir]
             got = np.moveaxis(after[a].reshape(19, 8, 8, 8), 0, -1)
             cells = ct[8:16, 8:16, 8:16] == 0
-            np.testing.assert_allclose(got[cells], want[cells], rtol=2e-5,
-                                       atol=2e-6 * np.abs(want[cells]).max())
+            if rho_tol is None:
+                np.testing.assert_allclose(got[cells], want[cells], rtol=2e-5,
+                                           atol=2e-6 * np.abs(want[cells]).max())
+            else:
+                rho = want[cells].sum(axis=-1, keepdims=True)
+                err = float((np.abs(got[cells] - want[cells]) / rho).max())
+                print(f"block {b} comp {a}: max |f - f_oracle| / rho = {err:.3g}")
+                assert err <= rho_tol
 
 
 def interior_meshed_blocks(gpu, case, count, seed=0):
@@ -193,20 +203,29 @@ def interior_meshed_blocks(gpu, case, count, seed=0):
     return picks
 
 
-@pytest.mark.parametrize("streaming", ["ab", "aa"])
-def test_full_size_injection_sampled_one_step(L, streaming):
+# one step of the 16-bit forms from the same decoded inputs: the rounding of
+# the stored deviations (measured: FP16 7.4e-6, BF16 1.6e-4 of the density)
+FULL_FORMS = {"fp32": None, "fp16": 5e-5, "bf16": 1e-3}
+
+
+@pytest.mark.parametrize("streaming,storage", [("ab", "fp32"), ("aa", "fp32"), ("ab", "fp16"),
+                                               ("ab", "bf16")])
+def test_full_size_injection_sampled_one_step(L, streaming, storage):
     """256^3 porous injection in the benchmark's launch configuration: after
-    300 steps (slots renumbered in block order on the way, A-B), one further
-    step of sampled interior blocks equals the oracle's step from the same
-    populations; the meshed set stays connected."""
+    300 steps (the mesh still growing; slots renumbered on the way, A-B) and
+    again after 900 (the meshed set at its final 58 %), one further step of 6
+    sampled interior blocks equals the oracle's step from the same
+    populations; the meshed set stays connected.  The 16-bit forms are
+    compared within one rounding of the stored deviation."""
     case = W.porous_injection()
-    gpu = gpu_of(L, case, streaming=streaming)
-    gpu.step(300)
-    if streaming == "ab":
-        assert gpu.stats()["slot_sorts"] > 0
-    picks = interior_meshed_blocks(gpu, case, 4)
-    assert len(picks) >= 2
-    one_step_sample(L, gpu, case, picks)
+    gpu = gpu_of(L, case, streaming=streaming, storage=storage)
+    for at, seed in ((300, 0), (900, 1)):
+        gpu.step(at - gpu.stats()["steps"])
+        if streaming == "ab":
+            assert gpu.stats()["slot_sorts"] > 0
+        picks = interior_meshed_blocks(gpu, case, 6, seed=seed)
+        assert len(picks) >= 4
+        one_step_sample(L, gpu, case, picks, rho_tol=FULL_FORMS[storage])
     act = set(gpu.active_blocks().tolist())
     nbx = nby = 32
     for b in act:
