@@ -293,10 +293,8 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * next; calls that overlap on the same GPU (other streams or host threads)
  * race on it and must be serialised by the caller.  Each call looks up the
  * array's device address on the current device (cudaGetSymbolAddress), so
- * the address stays valid after a cudaDeviceReset; the first call on a
- * device also loads the library's device code there, so make that first call
- * before any stream capture.  Errors: LBM_EINVAL, LBM_ECUDA (message in
- * lbm_last_error(NULL)). */
+ * the address stays valid after a cudaDeviceReset.  Errors: LBM_EINVAL,
+ * LBM_ECUDA (message in lbm_last_error(NULL)). */
 int lbm_mass_noalloc(const float *f, const uint32_t *solid, long long nblocks, int ncomp,
                      double *mass, void *stream);
 
