@@ -635,16 +635,22 @@ template <int ST, class Sink>
 __device__ __forceinline__ void dev_consume2(const DevLoad &L, const float2 wref[3],
                                              const float2 famb[3], Sink &&sink)
 {
-    auto one = [&]<int I>() {
-        const float2 x = Store<ST>::dec2(L.v[I]);
-        const bool amb = (L.ambs >> I) & 1u;
-        sink.template operator()<I>(add2(x, sel2(amb, famb[wclass(I)], wref[wclass(I)])));
+    auto all = [&](auto amb_of) {
+        auto one = [&]<int I>() {
+            const float2 x = Store<ST>::dec2(L.v[I]);
+            sink.template operator()<I>(add2(x, sel2(amb_of(I), famb[wclass(I)], wref[wclass(I)])));
+        };
+        one.template operator()<0>();
+        Unroll<0, NPAIR>::run([&]<int P>() {
+            one.template operator()<pair_rep(P)>();
+            one.template operator()<opp(pair_rep(P))>();
+        });
     };
-    one.template operator()<0>();
-    Unroll<0, NPAIR>::run([&]<int P>() {
-        one.template operator()<pair_rep(P)>();
-        one.template operator()<opp(pair_rep(P))>();
-    });
+    // warp-uniform: most warps have no ambient source, and skip the selects
+    if (__any_sync(FULL, L.ambs != 0u))
+        all([&](int i) { return ((L.ambs >> i) & 1u) != 0u; });
+    else
+        all([](int) { return false; });
 }
 
 // ---- A-A streaming: addressing (FP32, two components) ----------------------
@@ -1862,10 +1868,13 @@ __global__ void __launch_bounds__(THREADS) k_collide(KParams kp)
 // forces() for both components at once (same terms, paired arithmetic):
 // F[d] = (F_0, F_1) along axis d.  The mac copy in use starts at kp.mac +
 // moff.  All lanes must call; `live` masks the loads.
+// rn (optional): rn[D * THREADS] receives the density pair used for the
+// neighbour x + e_D (the cell's own behind a solid neighbour), for the
+// 16-bit collision's encode.
 template <int NC>
 __device__ __forceinline__ void forces2(const KParams &kp, const WarpNbr &wn, uint32_t moff, int slot,
                                         int c, int lx, int ly, int lz, uint32_t bits, bool live,
-                                        float2 rho, float2 F[3])
+                                        float2 rho, float2 F[3], float2 *rn = nullptr)
 {
     const float psi_c = live ? kp.mac[(size_t)moff + (size_t)slot * CELLS + c].z : 0.f;
     const float2 pc = make_float2(psi_c, psi_c * psi_c);
@@ -1885,6 +1894,7 @@ __device__ __forceinline__ void forces2(const KParams &kp, const WarpNbr &wn, ui
             const bool solid_n = (bits >> opp(D)) & 1u;  // x + e_D = x - e_opp(D)
             const float4 m = live ? __ldg(kp.mac + mb + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
             r_n[H] = sel2(solid_n, rho, make_float2(m.x, m.y));
+            if (rn) rn[D * THREADS] = r_n[H];
             p_n[H] = sel2(solid_n, pc, make_float2(m.z, m.z * m.z));
             s_n[H] = solid_n ? 1.f : 0.f;
         });
@@ -3183,7 +3193,9 @@ __device__ __forceinline__ void collide_dev_body(const KParams &kp, int step)
     uint32_t *wr = pops<ST>(kp) + (size_t)(par ^ 1) * kp.buf_stride;
     const uint32_t moff = (uint32_t)(par * kp.mac_stride);
     const float4 *mac_prev = kp.mac + (size_t)(par ^ 1) * kp.mac_stride;
-    const float2 *mac2 = reinterpret_cast<const float2 *>(kp.mac);  // (rho0, rho1) at 2 i
+    // the readers' density pairs of this thread's cell, kept by the force
+    // gather (each thread reads back only its own column: no barrier)
+    __shared__ float2 rn_s[Q][THREADS];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctrl->cell_updates += (unsigned long long)n * CELLS;
         ctrl->fluid_updates += ctrl->fluid_active;
@@ -3237,7 +3249,7 @@ __device__ __forceinline__ void collide_dev_body(const KParams &kp, int step)
 #pragma unroll
                 for (int d = 0; d < 3; ++d) u[d].y = 0.f;
             float2 F[3];
-            forces2<NC>(kp, cur.wn, moff, slot, c, lx, ly, lz, bits, nonsolid, rho, F);
+            forces2<NC>(kp, cur.wn, moff, slot, c, lx, ly, lz, bits, nonsolid, rho, F, &rn_s[0][threadIdx.x]);
             // Eqs. 10-12 with tau = 1 (f* = f_eq(rho, u + F / rho)), else
             // f* = f_eq(rho, u + F / rho) + (1 - 1/tau) (f - f_eq(rho, u));
             // every lane runs it (its shuffles need the whole warp), solid
@@ -3268,11 +3280,9 @@ __device__ __forceinline__ void collide_dev_body(const KParams &kp, int step)
                     const float2 e0 = mul2(wrho[wclass(I)], fma2(eu, fma2(eu, splat(4.5f), splat(3.f)), cu));
                     f = fma2(relax, sub2(fin[I], e0), f);
                 }
-                // the reader's density: the neighbour's, or the cell's own
-                const int tx = lx + cx(I), ty = ly + cy(I), tz = lz + cz(I);
-                const uint32_t mb = __shfl_sync(FULL, cur.wn.mbase, nbk(tx, ty, tz));
-                const bool solid_n = (bits >> opp(I)) & 1u;  // x + e_I = x - e_opp(I)
-                const float2 rr = (solid_n || !nonsolid) ? rho : __ldg(mac2 + 2 * (mb + lcell(tx, ty, tz)));
+                // the reader's density: the neighbour's (kept by the force
+                // gather), or the cell's own
+                const float2 rr = nonsolid ? rn_s[I][threadIdx.x] : rho;
                 const float2 d = fma2(splat(-wgt(I)), rr, f);
                 const uint32_t h = S::enc2(d.x, d.y);
                 if (nonsolid) dst[I * CELLS] = h;
