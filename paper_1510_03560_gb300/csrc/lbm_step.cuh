@@ -357,6 +357,26 @@ __device__ uint32_t cell_bits(const KParams &kp, int gid, int c)
     return bits;
 }
 
+// The same word with the 27 neighbour block ids given one per lane (lane k:
+// block k of the 27 around gid, -1 outside a non-periodic axis; lane 13:
+// gid), so that no lane recomputes them per direction.  Every lane of the
+// warp calls (shuffles).
+__device__ __forceinline__ uint32_t cell_bits_nbr(const KParams &kp, int gid, int nid_lane, int c)
+{
+    const int lx = lx_of(c), ly = ly_of(c), lz = lz_of(c);
+    uint32_t bits = 0;
+    Unroll<0, Q>::run([&]<int I>() {
+        const int sx = lx - cx(I), sy = ly - cy(I), sz = lz - cz(I);
+        const int k = nbk(sx, sy, sz), lc = lcell(sx, sy, sz);
+        const int nid = __shfl_sync(FULL, nid_lane, k);
+        const bool solid =
+            nid < 0 || ((kp.solid[(size_t)nid * MASK_WORDS + (lc >> 5)] >> (lc & 31)) & 1u);
+        bits |= (uint32_t)solid << I;
+    });
+    if ((kp.held[(size_t)gid * MASK_WORDS + (c >> 5)] >> (c & 31)) & 1u) bits |= 1u << HELD_BIT;
+    return bits;
+}
+
 // Source offset (in the read buffer) of the population moving along e_I
 // into cell c: from x - e_I; the cell's own opposite population behind a
 // solid cell (halfway bounce-back); its own population at held cells.
@@ -1627,7 +1647,15 @@ __device__ __forceinline__ void activate_body(const KParams &kp, int step)
             prepared = *(volatile const unsigned *)&kp.prep[gid];
             __threadfence();
         }
-        const uint32_t bits = prepared ? __ldcg(kp.nbits_pre + (size_t)gid * CELLS + c) : cell_bits(kp, gid, c);
+        // (prepared is the same for the whole warp: one load of one word)
+        uint32_t bits;
+        if (prepared) {
+            bits = __ldcg(kp.nbits_pre + (size_t)gid * CELLS + c);
+        } else {
+            const int lane = threadIdx.x & 31;
+            const int nid_lane = lane == 13 ? gid : (lane < 27 ? neighbour_of(kp, gid, lane) : -1);
+            bits = cell_bits_nbr(kp, gid, nid_lane, c);
+        }
         if (c == 0) {
             kp.act_step[gid] = step + 1;
             if (prepared) atomicAdd(&ctrl->prepared_hits, 1ull);
@@ -3767,9 +3795,9 @@ struct Launch {
     {
         // (the candidates were renumbered in block order by the pass-1 launch)
         if (kp.ncomp == 2)
-            k_activate<2, ST><<<sms, THREADS, 0, s>>>(kp);
+            k_activate<2, ST><<<2 * sms, THREADS, 0, s>>>(kp);
         else
-            k_activate<1, ST><<<sms, THREADS, 0, s>>>(kp);
+            k_activate<1, ST><<<2 * sms, THREADS, 0, s>>>(kp);
         return cudaGetLastError();
     }
     static cudaError_t collide(const KParams &kp, int step, int sms, cudaStream_t s)
