@@ -208,17 +208,20 @@ def interior_meshed_blocks(gpu, case, count, seed=0):
 FULL_FORMS = {"fp32": None, "fp16": 5e-5, "bf16": 1e-3}
 
 
-@pytest.mark.parametrize("streaming,storage", [("ab", "fp32"), ("aa", "fp32"), ("ab", "fp16"),
-                                               ("ab", "bf16")])
-def test_full_size_injection_sampled_one_step(L, streaming, storage):
+@pytest.mark.parametrize("streaming,storage,option", [("ab", "fp32", None), ("aa", "fp32", None),
+                                                      ("ab", "fp16", None), ("ab", "bf16", None),
+                                                      ("ab", "fp32", "partials"), ("ab", "fp32", "fusion")])
+def test_full_size_injection_sampled_one_step(L, streaming, storage, option):
     """256^3 porous injection in the benchmark's launch configuration: after
     300 steps (the mesh still growing; slots renumbered on the way, A-B) and
     again after 900 (the meshed set at its final 58 %), one further step of 6
     sampled interior blocks equals the oracle's step from the same
     populations; the meshed set stays connected.  The 16-bit forms are
-    compared within one rounding of the stored deviation."""
+    compared within one rounding of the stored deviation.  The two
+    single-read options (density partials, fused step) run the same check."""
     case = W.porous_injection()
-    gpu = gpu_of(L, case, streaming=streaming, storage=storage)
+    over = {"partials": {"partials": True}, "fusion": {"fusion": (True, 0)}}.get(option, {})
+    gpu = gpu_of(L, case, streaming=streaming, storage=storage, **over)
     for at, seed in ((300, 0), (900, 1)):
         gpu.step(at - gpu.stats()["steps"])
         if streaming == "ab":
