@@ -42,9 +42,11 @@
 //              adhesion) from the neighbours' mac + forced BGK collision
 //              (Eqs. 10-12) -> f of the other buffer
 // (or, fused, k_fused2: the collision of a step and k_macro's work for the
-// next one in a single launch, see below)
+// next one in a single launch; or, with the density partials, a collision
+// that also sums the next step's densities and a pass 1 split into
+// k_macro2p / k_macro2f that adds them; see below)
 // Between steps, now and then, the k_sort_* launches renumber the meshed
-// slots in block order (locality; "slot order" below).  Further sections:
+// slots in the slot order (locality; "slot order" below).  Further sections:
 // A-A streaming (one population array, Sec. 3), the TMA-staged and
 // deviation-form kernels, the cooperative multi-step kernel.  The file is
 // compiled once per storage form and, for FP32, once per block shape.
