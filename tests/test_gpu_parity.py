@@ -214,7 +214,8 @@ FULL_FORMS = {"fp32": None, "fp16": 5e-5, "bf16": 1e-3}
 
 @pytest.mark.parametrize("streaming,storage,option", [("ab", "fp32", None), ("aa", "fp32", None),
                                                       ("ab", "fp16", None), ("ab", "bf16", None),
-                                                      ("ab", "fp32", "partials"), ("ab", "fp32", "fusion")])
+                                                      ("ab", "fp32", "partials"), ("ab", "fp32", "fusion"),
+                                                      ("ab", "fp32", "c2")])
 def test_full_size_injection_sampled_one_step(L, streaming, storage, option):
     """256^3 porous injection in the benchmark's launch configuration: after
     300 steps (the mesh still growing; slots renumbered on the way, A-B) and
@@ -222,8 +223,11 @@ def test_full_size_injection_sampled_one_step(L, streaming, storage, option):
     sampled interior blocks equals the oracle's step from the same
     populations; the meshed set stays connected.  The 16-bit forms are
     compared within one rounding of the stored deviation.  The two
-    single-read options (density partials, fused step) run the same check."""
-    case = W.porous_injection()
+    single-read options (density partials, fused step) run the same check,
+    and so does the 384^3 injection (the largest configuration; its slot
+    strips of 10 block rows leave a ragged last strip of 8)."""
+    case = W.porous_injection() if option != "c2" else W.porous_injection(
+        n=(384, 384, 384), seed=1510035602, inlet=96, x_free=24)
     over = {"partials": {"partials": True}, "fusion": {"fusion": (True, 0)}}.get(option, {})
     gpu = gpu_of(L, case, streaming=streaming, storage=storage, **over)
     for at, seed in ((300, 0), (900, 1)):
@@ -234,7 +238,7 @@ def test_full_size_injection_sampled_one_step(L, streaming, storage, option):
         assert len(picks) >= 4
         one_step_sample(L, gpu, case, picks, rho_tol=FULL_FORMS[storage])
     act = set(gpu.active_blocks().tolist())
-    nbx = nby = 32
+    nbx, nby = case["params"]["nx"] // 8, case["params"]["ny"] // 8
     for b in act:
         bx, by, bz = b % nbx, (b // nbx) % nby, b // (nbx * nby)
         nbs = [(bx + dx) + nbx * ((by + dy) + nby * (bz + dz))
